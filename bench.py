@@ -1,0 +1,330 @@
+"""Throughput of the fused two-component Shan-Chen step on GB300.
+
+Workload: D3Q19, 128^3 periodic, symmetric interactions (G_AA = G_BB = 0),
+spherical A-rich droplet of radius 24 (tanh profile, +/-1e-3 seeded noise),
+FP32 deviation storage.  One benchmark step = 2048 fused time steps (the
+convergence-check interval delta t = 2^11 of the paper's section 4) followed by
+the radial pressure-tensor profile (0.5 lattice-unit bins), the bulk pressure
+at the centre node and at the far corner, and the sigma[R] minimum -- every
+stage of the hot path, all in this library's kernels.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on the same workload (a bounded sample per step) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % of HBM roofline (D3Q19 2-comp); FP32 vs FP16-storage at stated σ error"
+SHAPE = (128, 128, 128)
+RADIUS = 24.0
+G_CROSS = 3.6  # G c_s^2 = 1.2: the largest tested coupling that is stable in three dimensions at tau = 1
+INNER = 2048  # time steps per benchmark step (section 4: delta t = 2^11)
+BYTES_PER_SITE = {"f32": 304, "f16": 152, "bf16": 152, "f64": 608}  # 2 comps x 19 pops x (read + write) x bytes
+
+
+def workload_config(storage: str):
+    return {
+        "workload": f"D3Q19 two-component Shan-Chen, 128^3 periodic droplet R=24, symmetric G (G c_s^2 = 1.2), "
+                    f"tau = 1, {storage.upper()} deviation storage; {INNER} fused steps + radial P-tensor "
+                    f"profile + sigma[R] minimum per step",
+        "lattice": "D3Q19",
+        "sites": SHAPE[0] * SHAPE[1] * SHAPE[2],
+        "time_steps_per_step": INNER,
+        "storage": storage,
+        "l2": "inputs larger than L2 (two population buffers of 2*19*128^3*4 B = 319 MB each)",
+    }
+
+
+def fields():
+    import sc_synth
+
+    return sc_synth.droplet(SHAPE[::-1], (64, 64, 64), RADIUS, n_in=0.95, n_out=0.05, amplitude=1e-3)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(budget_s: float = 12.0, shape=(64, 64, 64)):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample:
+    the same droplet workload scaled to 64^3 (R = 12), steps until the budget."""
+    import oracle
+    import sc_synth
+
+    op = oracle.Params(shape=shape, lattice=oracle.D3Q19, psi_self=oracle.PSI_EXP, G=G_CROSS)
+    nA, nB = sc_synth.droplet(shape[::-1], tuple(s // 2 for s in shape), RADIUS * shape[0] / SHAPE[0])
+    f = oracle.init(op, nA, nB)
+    oracle.step(op, f, 1)  # warm
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        f = oracle.step(op, f, 2)
+        n += 2
+    dt = time.perf_counter() - t0
+    sites = shape[0] * shape[1] * shape[2]
+    return {"value": sites * n / dt / 1e6, "unit": "MLUPS", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{n} FP64 oracle time steps of the same droplet workload at {shape[0]}^3 (R = "
+                      f"{RADIUS * shape[0] / SHAPE[0]:g}), {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """The oracle arm: rank 0 only, FP64 on the host cores, same metric and unit."""
+    if rank != 0:
+        return
+    import oracle
+    import oracle.sigma as SG
+    import sc_synth
+
+    shape = SHAPE
+    op = oracle.Params(shape=shape, lattice=oracle.D3Q19, psi_self=oracle.PSI_EXP, G=G_CROSS)
+    nA, nB = fields()
+    f = oracle.init(op, nA, nB)
+    sample = 2  # oracle time steps per benchmark step (bounded sample of the 2048)
+    sites = shape[0] * shape[1] * shape[2]
+
+    def one():
+        nonlocal f
+        f = oracle.step(op, f, sample)
+        a, b, _ = oracle.moments(op, f, with_u=False)
+        rows = oracle.profile(op, a, b, oracle.RADIAL, (64, 64, 64), 0.5, 128)
+        r, _, pt, _, _ = SG.clean_profile(rows)
+        c = 64 + 128 * (64 + 128 * 64)
+        SG.surface_of_tension(r, pt, oracle.bulk_pressure(op, a[c], b[c]), oracle.bulk_pressure(op, a[-1], b[-1]))
+
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    dt = time.perf_counter() - t0
+    value = sites * sample * args.steps / dt / 1e6
+    line = {"metric": METRIC, "value": value, "unit": "MLUPS", "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(workload_config("f64"), time_steps_per_step=sample),
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": oracle.threads(), "kind": "oracle",
+                             "sample": f"{sample} FP64 oracle time steps at 128^3 + radial profile + sigma[R] "
+                                       f"minimum per step"},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+
+    from paper_2112_02574_gb300 import binding as B
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    storage = args.storage
+    st = {"f32": B.SC_STORE_F32, "f16": B.SC_STORE_F16, "bf16": B.SC_STORE_BF16, "f64": B.SC_STORE_F64}[storage]
+    params = B.make_params(SHAPE, lattice=B.SC_D3Q19, stencil=B.SC_FORCE_E4, psi_self=B.SC_PSI_EXP, storage=st,
+                           tau=(1.0, 1.0), G=G_CROSS, G_self=(0.0, 0.0), tile_y=args.tile_y, tile_z=args.tile_z)
+    nA0, nB0 = fields()
+    stream = torch.cuda.Stream(dev)
+    sites = SHAPE[0] * SHAPE[1] * SHAPE[2]
+    with torch.cuda.stream(stream):
+        sim = B.Simulation(params, nA0, nB0, device=dev, stream=stream)
+        rows = torch.empty(128 * 6, dtype=torch.float64, device=dev)
+        pio = torch.empty(2, dtype=torch.float64, device=dev)
+        sig = torch.empty(8, dtype=torch.float64, device=dev)
+    centre = (64.0, 64.0, 64.0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    step_ms = []
+
+    def one(record=False):
+        if record:
+            ev[0].record(stream)
+        B.sc_step(sim.ctx, INNER)
+        if record:
+            ev[1].record(stream)
+        B.sc_pressure_profile(sim.ctx, B.SC_PROFILE_RADIAL, centre, 0.5, 128, rows)
+        B.sc_bulk_pressure_at(sim.ctx, (64, 64, 64), pio[0:1])
+        B.sc_bulk_pressure_at(sim.ctx, (127, 127, 127), pio[1:2])
+        B.sc_sigma_minimum(rows.view(128, 6), pio, 3, 0.01, 64.0, 0.01, sig, stream)
+        if record:
+            ev[1].synchronize()
+            step_ms.append(ev[0].elapsed_time(ev[1]))
+
+    for _ in range(args.warmup):
+        one()
+    B.sc_sync(sim.ctx)
+    launches0 = sim.launches
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        if dist:
+            tdist.barrier()
+        torch.cuda.synchronize(dev)
+        start.record(stream)
+        for _ in range(args.steps):
+            one(record=args.kernel_events)
+        stop.record(stream)
+        torch.cuda.synchronize(dev)
+        if dist:
+            tdist.barrier()
+    B.sc_sync(sim.ctx)
+    ms = start.elapsed_time(stop)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    step_launches = sim.launches - launches0
+    # per bench step: INNER fused steps + fields + profile partials + profile finalise + 2 bulk + sigma
+    launches = step_launches + args.steps * 6
+
+    # kernel-only timing of the fused step (events around the INNER launches, separate pass)
+    if not step_ms:
+        for _ in range(3):
+            one(record=True)
+    kern_ms = statistics.median(step_ms) / INNER
+    alg_bytes = BYTES_PER_SITE[storage] * sites
+    peak, peak_kind = measured_peak()
+    achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
+
+    value = sites * INNER * args.steps * world / (ms * 1e-3) / 1e6
+
+    # end to end through the host-buffer entry point: H2D of the initial fields, INNER steps, D2H of the densities
+    e2e = None
+    if rank == 0 or True:
+        ws = sim.workspace  # reuse the device workspace (the simulation above is finished)
+        hA = torch.from_numpy(nA0.reshape(-1)).pin_memory()
+        hB = torch.from_numpy(nB0.reshape(-1)).pin_memory()
+        oA, oB = torch.empty_like(hA).pin_memory(), torch.empty_like(hB).pin_memory()
+        with torch.cuda.stream(stream):
+            B.sc_run_host(params, hA, hB, INNER, oA, oB, ws, stream)  # warm
+            t0 = time.perf_counter()
+            reps = max(1, args.steps // 2)
+            for _ in range(reps):
+                B.sc_run_host(params, hA, hB, INNER, oA, oB, ws, stream)
+            e2e_s = (time.perf_counter() - t0) / reps
+        e2e = {"value": sites * INNER * world / e2e_s / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": 2 * sites * 8, "d2h_bytes_per_step": 2 * sites * 8,
+               "note": f"sc_run_host per step: H2D of n_A0, n_B0 (FP64), create, {INNER} steps, D2H of n_A, n_B"}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": storage, "data": "synthetic", "config": workload_config(storage),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "sc_step_kernel", "bytes_per_site": BYTES_PER_SITE[storage],
+                     "kernel_ms": kern_ms, "peak_source": peak_kind},
+        "hbm_roofline_mlups_frac": value / world * 1e6 * BYTES_PER_SITE[storage] / (peak * 1e9),
+        "gpu_launches": launches, "clocks": clk.summary(), "e2e": e2e,
+        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "f64"])
+    ap.add_argument("--tile-y", type=int, default=0)
+    ap.add_argument("--tile-z", type=int, default=0)
+    ap.add_argument("--kernel-events", action="store_true", help="record per-step kernel events in the timed loop")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl")
+    try:
+        run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as tdist
+
+            tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

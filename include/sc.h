@@ -1,0 +1,181 @@
+/*
+ * sc.h -- C ABI of a GB300 (sm_103a) library for the two-component Shan-Chen
+ * lattice Boltzmann method and the surface-of-tension analysis of
+ * Lulli et al., "Mesoscale Modelling of the Tolman Length in Multi-component
+ * Systems" (arXiv:2112.02574).
+ *
+ * Conventions for every entry point
+ *   - Return value: sc_status.  Nothing here aborts, exits or throws.  On an
+ *     error the entry point returns before launching any work, and
+ *     sc_last_error() describes the failure (a per-thread message).
+ *   - Memory: the caller owns every buffer (inputs, outputs, workspace).  A
+ *     pointer documented as "device" must be CUDA device memory on the current
+ *     device, "host" must be host memory (pinned or pageable).  The library
+ *     allocates no device memory except where an entry point says so; its
+ *     context (sc_ctx) is a small host object holding offsets into the caller's
+ *     workspace.
+ *   - Streams: all device work of a context is issued on the stream given to
+ *     sc_create (a cudaStream_t passed as void*; NULL = legacy default stream)
+ *     and is asynchronous unless the entry point says it synchronises.
+ *   - Lattice fields are [nz][ny][nx] with x fastest; site s = x + nx*(y + ny*z);
+ *     every direction is periodic.
+ *   - Populations in the "natural" FP64 layout are f[J][i][s], J = 0 (A), 1 (B),
+ *     i in the velocity order below, and hold the pre-collision populations
+ *     f_i^J(x, t) of Eq. lbm.
+ *   - Units are lattice units; c_s^2 = 1/3 (section 2 and section 4).
+ *
+ * Velocity order (opposite directions adjacent):
+ *   D3Q19: 0 (0,0,0); 1..6 (+x)(-x)(+y)(-y)(+z)(-z);
+ *          7 (1,1,0) 8 (-1,-1,0) 9 (1,-1,0) 10 (-1,1,0) 11 (1,0,1) 12 (-1,0,-1)
+ *          13 (1,0,-1) 14 (-1,0,1) 15 (0,1,1) 16 (0,-1,-1) 17 (0,1,-1) 18 (0,-1,1)
+ *   D2Q9:  0 (0,0); 1..4 (+x)(-x)(+y)(-y); 5 (1,1) 6 (-1,-1) 7 (1,-1) 8 (-1,1)
+ */
+#ifndef SC_H
+#define SC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SC_OK = 0,
+  SC_EINVAL = 1,        /* bad argument (null pointer, size, parameter out of range) */
+  SC_ENOMEM = 2,        /* workspace smaller than sc_workspace_bytes() */
+  SC_ECUDA = 3,         /* a CUDA runtime call failed (message has the CUDA error) */
+  SC_ENAN = 4,          /* a kernel met a non-positive or non-finite density */
+  SC_ETIMEOUT = 5,      /* a bounded device-side wait ran out */
+  SC_EUNSUPPORTED = 6   /* valid request this build does not implement */
+} sc_status;
+
+typedef enum { SC_D2Q9 = 0, SC_D3Q19 = 1 } sc_lattice;
+/* Forcing stencil of Eq. sc_force: E4 = the velocity set's own non-rest vectors
+ * with W(1) = 1/6, W(2) = 1/12 (section 2; D2Q9: 1/3, 1/12); E6 = all integer
+ * vectors with |xi|^2 = 1..4 and W = 2/15, 1/15, 1/60, 1/120 (D3Q19 only). */
+typedef enum { SC_FORCE_E4 = 0, SC_FORCE_E6 = 1 } sc_stencil;
+/* Pseudopotential of the self-coupling term: psi = n, or psi = exp(-1/n) (section 4). */
+typedef enum { SC_PSI_N = 0, SC_PSI_EXP = 1 } sc_psi;
+/* Population storage.  Stored values are deviations g_i = f_i - w_i nbar_J from
+ * a rest equilibrium with the mean initial density nbar_J; F16/BF16 store
+ * g_i * 2^k(J,i) with a power-of-two scale fixed at sc_create.  Collision
+ * arithmetic is FP32 for F32/F16/BF16 and FP64 for F64. */
+typedef enum { SC_STORE_F32 = 0, SC_STORE_F16 = 1, SC_STORE_BF16 = 2, SC_STORE_F64 = 3 } sc_storage;
+typedef enum { SC_PROFILE_RADIAL = 0, SC_PROFILE_PLANAR_Z = 1, SC_PROFILE_AXIS_X = 2 } sc_profile_kind;
+
+/* Model and layout parameters.  Couplings follow Eq. sc_force literally:
+ * F_A = -G c_s^2 n_A sum_a W n_B(x+xi_a) xi_a - G_AA c_s^2 psi_A sum_a W psi_A(x+xi_a) xi_a. */
+typedef struct {
+  int32_t nx, ny, nz;  /* lattice size, each >= 1; nz == 1 for D2Q9 */
+  int32_t lattice;     /* sc_lattice */
+  int32_t stencil;     /* sc_stencil */
+  int32_t psi_self;    /* sc_psi */
+  int32_t storage;     /* sc_storage */
+  int32_t tile_y;      /* step-kernel tile rows (1, 2, 4 or 8); 0 = library default */
+  int32_t tile_z;      /* planes per step-kernel block (>= 1); 0 = library default */
+  int32_t reserved;    /* must be 0 */
+  double tau[2];       /* tau_A, tau_B > 1/2 (Eq. omega_i) */
+  double G;            /* inter-component coupling G */
+  double G_self[2];    /* self couplings G_AA, G_BB */
+} sc_params;
+
+typedef struct sc_ctx sc_ctx;
+
+/* Bytes of device workspace sc_create needs for these parameters (0 if the
+ * parameters are invalid).  Layout: two population buffers, FP64 field planes
+ * for the analysis kernels, reduction scratch and a status word. */
+size_t sc_workspace_bytes(const sc_params *params);
+
+/* Create a simulation (section 2; initial state of section 4: rest equilibrium
+ * f_i = w_i n_J with u = 0).  nA0, nB0: device FP64 [N] initial densities
+ * (each > 0).  workspace: device memory of ws_bytes >= sc_workspace_bytes(),
+ * 256-byte aligned, owned by the caller and kept alive until sc_destroy.
+ * Enqueues the initialisation on `stream` and synchronises it. */
+sc_status sc_create(const sc_params *params, const double *nA0, const double *nB0, void *workspace,
+                    size_t ws_bytes, void *stream, sc_ctx **out);
+
+/* Advance nsteps >= 0 time steps of Eq. lbm (BGK of Eq. omega_i, Guo forcing,
+ * equilibrium of Eq. feq, common velocity of Eq. u, force of Eq. sc_force,
+ * streaming).  One fused kernel launch per step; asynchronous. */
+sc_status sc_step(sc_ctx *ctx, int64_t nsteps);
+
+/* Densities n_A, n_B (device FP64 [N] each) and, if u != NULL, the common
+ * velocity of Eq. u (device FP64 [3][N], force included).  Asynchronous. */
+sc_status sc_moments(sc_ctx *ctx, double *nA, double *nB, double *u);
+
+/* Pre-collision populations in the natural FP64 layout (device [2][Q][N]). */
+sc_status sc_get_populations(sc_ctx *ctx, double *f);
+/* Replace the state by natural-layout FP64 populations (device [2][Q][N]);
+ * values are rounded to the storage format. */
+sc_status sc_set_populations(sc_ctx *ctx, const double *f);
+
+/* Raw state (checkpoint / resume, bit-exact): bytes == sc_state_bytes(ctx);
+ * dst / src are device memory. */
+size_t sc_state_bytes(const sc_ctx *ctx);
+sc_status sc_get_state(sc_ctx *ctx, void *dst, size_t bytes);
+sc_status sc_set_state(sc_ctx *ctx, const void *src, size_t bytes);
+
+/* Pressure-tensor profile (Eq. sm:pt, accumulated in FP64).  out: device FP64
+ * [nbins][6] rows (coordinate, P_N, P_T, n_A, n_B, count), means per bin,
+ * empty bins all zero.
+ *   RADIAL:   shells of width bin_width around centre (minimum image), P_N =
+ *             rhat.P.rhat, P_T = (tr P - P_N)/(d - 1), at r = 0 both tr P/d
+ *             (decomposition of Eq. pt_projection, section 3);
+ *   PLANAR_Z: one bin per plane z < nbins, P_N = <P^zz>, P_T = <(P^xx+P^yy)/2>
+ *             (flat interface, section 4);
+ *   AXIS_X:   sites (cx + k, cy, cz), k < nbins, P_N = P^xx, P_T = P^yy
+ *             (section 3, the paper's own estimator).
+ * Deterministic: per-block partial sums in a fixed order.  Asynchronous. */
+sc_status sc_pressure_profile(sc_ctx *ctx, int32_t kind, const double centre[3], double bin_width, int32_t nbins,
+                              double *out);
+
+/* Bulk pressure of Eq. bulkp at one node; out: device FP64 [1].  Asynchronous. */
+sc_status sc_bulk_pressure_at(sc_ctx *ctx, const int32_t node[3], double *out);
+
+/* Generalized surface tension minimum from a profile (section 3, Eqs.
+ * gen_sigma, gen_d_sigma), in FP64 on the device.  rows: device FP64
+ * [nbins][6] as written by sc_pressure_profile; P_in_out: device FP64 [2].
+ * Integrals run over the non-empty rows up to the last one (r_max): the
+ * pressure-jump part exactly, P_T by the trapezoid rule, so that
+ * sigma[R] = dP R/3 + C/R^2 (dim 3) or dP R/2 + C/R (dim 2) with
+ * C = int_0^r_max r^(dim-1) (P_out - P_T) dr.  out: device FP64 [8] =
+ * (dP, C, R_s, sigma_s, R_grid, sigma_grid, P_in, P_out) where R_s is the
+ * closed-form minimum, sigma_s = dP R_s / 2 (dim 3) or dP R_s (dim 2), and
+ * (R_grid, sigma_grid) the parabolic interpolation of the minimum of sigma[R]
+ * sampled on [R_lo, R_hi] with step R_step (the paper's procedure).
+ * stream: cudaStream_t as void*.  Asynchronous. */
+sc_status sc_sigma_minimum(const double *rows, int32_t nbins, const double *P_in_out, int32_t dim, double R_lo,
+                           double R_hi, double R_step, double *out, void *stream);
+
+/* Conserved totals, FP64, deterministic: out device [5] = (mass_A, mass_B,
+ * momentum x, y, z) summed over the lattice (section 2).  Asynchronous. */
+sc_status sc_totals(sc_ctx *ctx, double *out);
+
+/* Wait for the context's stream and report device-side errors (SC_ENAN when a
+ * step met a non-positive or non-finite density; the flag is then cleared). */
+sc_status sc_sync(sc_ctx *ctx);
+
+/* Convenience entry point with HOST buffers: create, run nsteps and read the
+ * densities back.  nA0, nB0: host FP64 [N] in; nA, nB: host FP64 [N] out.
+ * The workspace is device memory as for sc_create.  Synchronous. */
+sc_status sc_run_host(const sc_params *params, const double *nA0, const double *nB0, int64_t nsteps, double *nA,
+                      double *nB, void *workspace, size_t ws_bytes, void *stream);
+
+/* Number of step-kernel launches issued by this context so far. */
+int64_t sc_kernel_launches(const sc_ctx *ctx);
+
+/* Mean initial densities nbar_J used as the storage reference (host out [2]). */
+sc_status sc_reference_density(const sc_ctx *ctx, double nbar[2]);
+
+/* Release the context (host memory only; the workspace stays the caller's). */
+void sc_destroy(sc_ctx *ctx);
+
+/* Last error message of the calling thread ("" if none). */
+const char *sc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SC_H */

@@ -100,6 +100,7 @@ def lib():
         L.orc_bulk_pressure.restype = ctypes.c_double
         L.orc_pressure_tensor.argtypes = [pp, dp, dp, dp]
         L.orc_profile.argtypes = [pp, dp, dp, ctypes.c_int, dp, ctypes.c_double, ctypes.c_int, dp]
+        L.orc_threads.argtypes = []
         _lib = L
     return _lib
 
@@ -111,6 +112,11 @@ def _dp(a: np.ndarray):
 
 def _flat(a) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+
+
+def threads() -> int:
+    """OpenMP threads the oracle's loops run on."""
+    return int(lib().orc_threads())
 
 
 def stencil(p: Params):

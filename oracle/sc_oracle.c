@@ -545,3 +545,11 @@ int orc_velocity_set(int lattice, int *xi_out /* [Q][3] */, double *w_out) {
   }
   return Q;
 }
+
+/* Threads the OpenMP loops above use. */
+#ifdef _OPENMP
+#include <omp.h>
+int orc_threads(void) { return omp_get_max_threads(); }
+#else
+int orc_threads(void) { return 1; }
+#endif

@@ -1,0 +1,573 @@
+// C ABI of the library (declared in include/sc.h): validation, workspace
+// layout, contexts, and the host side of every entry point.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "sc_aux.cuh"
+#include "sc_dispatch.h"
+
+using namespace scgb;
+
+namespace {
+
+thread_local std::string g_err;
+
+sc_status fail(sc_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define SC_CUDA(call)                                                                            \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) return fail(SC_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));       \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+constexpr size_t kPartialBytes = size_t(16) << 20;  // per-block partial sums of the reductions
+constexpr size_t kStatusBytes = 4096;                // status word + small scalars
+constexpr int kMaxPartialBlocks = 1024;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+int q_of(const sc_params *p) { return p->lattice == SC_D3Q19 ? 19 : 9; }
+size_t store_bytes(int storage) {
+  switch (storage) {
+    case SC_STORE_F32: return 4;
+    case SC_STORE_F16:
+    case SC_STORE_BF16: return 2;
+    case SC_STORE_F64: return 8;
+    default: return 0;
+  }
+}
+
+sc_status validate(const sc_params *p) {
+  if (!p) return fail(SC_EINVAL, "params is NULL");
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(SC_EINVAL, "lattice size must be >= 1 in every direction");
+  if ((int64_t)p->nx * p->ny * p->nz > (int64_t(1) << 31) - 1)
+    return fail(SC_EINVAL, "more than 2^31 - 1 sites is not supported");
+  if (p->lattice != SC_D2Q9 && p->lattice != SC_D3Q19) return fail(SC_EINVAL, "unknown lattice %d", p->lattice);
+  if (p->lattice == SC_D2Q9 && p->nz != 1) return fail(SC_EINVAL, "D2Q9 needs nz == 1");
+  if (p->stencil != SC_FORCE_E4 && p->stencil != SC_FORCE_E6) return fail(SC_EINVAL, "unknown stencil %d", p->stencil);
+  if (p->stencil == SC_FORCE_E6 && p->lattice != SC_D3Q19) return fail(SC_EINVAL, "the E6 stencil needs D3Q19");
+  if (p->psi_self != SC_PSI_N && p->psi_self != SC_PSI_EXP) return fail(SC_EINVAL, "unknown psi %d", p->psi_self);
+  if (store_bytes(p->storage) == 0) return fail(SC_EINVAL, "unknown storage %d", p->storage);
+  if (p->tile_y != 0 && p->tile_y != 1 && p->tile_y != 2 && p->tile_y != 4 && p->tile_y != 8)
+    return fail(SC_EINVAL, "tile_y must be 0, 1, 2, 4 or 8");
+  if (p->tile_z < 0) return fail(SC_EINVAL, "tile_z must be >= 0");
+  if (p->reserved != 0) return fail(SC_EINVAL, "reserved must be 0");
+  for (int J = 0; J < 2; ++J)
+    if (!(p->tau[J] > 0.5) || !isfinite(p->tau[J])) return fail(SC_EINVAL, "tau[%d] must be > 1/2", J);
+  if (!isfinite(p->G) || !isfinite(p->G_self[0]) || !isfinite(p->G_self[1]))
+    return fail(SC_EINVAL, "couplings must be finite");
+  return SC_OK;
+}
+
+struct Layout {
+  size_t pop_bytes;  // one population buffer
+  size_t off_pop[2], off_fields, off_partial, off_status, total;
+};
+
+Layout layout_of(const sc_params *p) {
+  Layout L;
+  const int64_t N = (int64_t)p->nx * p->ny * p->nz;
+  L.pop_bytes = (size_t)2 * q_of(p) * N * store_bytes(p->storage);
+  size_t off = 0;
+  L.off_pop[0] = off;
+  off = align_up(off + L.pop_bytes);
+  L.off_pop[1] = off;
+  off = align_up(off + L.pop_bytes);
+  L.off_fields = off;
+  off = align_up(off + (size_t)4 * N * sizeof(double));
+  L.off_partial = off;
+  off = align_up(off + kPartialBytes);
+  L.off_status = off;
+  off = align_up(off + kStatusBytes);
+  L.total = off;
+  return L;
+}
+
+int default_tile_y(const sc_params *p) { return p->tile_y ? p->tile_y : 4; }
+int default_tile_z(const sc_params *p) {
+  if (p->lattice == SC_D2Q9) return 1;
+  if (p->tile_z) return p->tile_z < p->nz ? p->tile_z : p->nz;
+  return p->nz < 16 ? p->nz : 16;
+}
+
+}  // namespace
+
+struct sc_ctx {
+  sc_params p;
+  int64_t N;
+  int Q;
+  cudaStream_t stream;
+  char *ws;
+  Layout L;
+  int cur;  // buffer holding the current state
+  int tile_y, tile_z;
+  double nbar[2], psibar[2];
+  double scale[2][19], inv_scale[2][19];
+  int64_t launches;
+  int64_t steps;
+  int64_t fields_at;  // step count the FP64 fields were computed at (-1: stale)
+};
+
+namespace {
+
+unsigned int *status_word(sc_ctx *c) { return reinterpret_cast<unsigned int *>(c->ws + c->L.off_status); }
+double *status_scalars(sc_ctx *c) { return reinterpret_cast<double *>(c->ws + c->L.off_status + 256); }
+double *fields_of(sc_ctx *c) { return reinterpret_cast<double *>(c->ws + c->L.off_fields); }
+double *partial_of(sc_ctx *c) { return reinterpret_cast<double *>(c->ws + c->L.off_partial); }
+
+PopArgs pop_args(sc_ctx *c, int buf) {
+  PopArgs a;
+  a.buf = c->ws + c->L.off_pop[buf];
+  a.nx = c->p.nx;
+  a.ny = c->p.ny;
+  a.nz = c->p.nz;
+  a.N = c->N;
+  for (int J = 0; J < 2; ++J) {
+    a.nbar[J] = c->nbar[J];
+    for (int i = 0; i < 19; ++i) {
+      a.scale[J][i] = c->scale[J][i];
+      a.inv_scale[J][i] = c->inv_scale[J][i];
+    }
+  }
+  return a;
+}
+
+ForceParams force_params(const sc_ctx *c) {
+  ForceParams f;
+  f.G = c->p.G;
+  f.G_self[0] = c->p.G_self[0];
+  f.G_self[1] = c->p.G_self[1];
+  f.nx = c->p.nx;
+  f.ny = c->p.ny;
+  f.nz = c->p.nz;
+  f.N = c->N;
+  return f;
+}
+
+int grid_for(int64_t n, int block) {
+  int64_t g = (n + block - 1) / block;
+  return (int)(g < 1 ? 1 : (g > 152 * 32 ? 152 * 32 : g));
+}
+
+// Dispatch on (lattice, storage) for the population-access kernels.
+#define SC_POP_DISPATCH(ctx, KERNEL, grid, block, smem, ...)                                             \
+  do {                                                                                                    \
+    const int lat_ = (ctx)->p.lattice, st_ = (ctx)->p.storage;                                           \
+    if (lat_ == SC_D3Q19) {                                                                               \
+      if (st_ == SC_STORE_F32) KERNEL<kD3Q19, float><<<grid, block, smem, (ctx)->stream>>>(__VA_ARGS__);  \
+      if (st_ == SC_STORE_F16) KERNEL<kD3Q19, __half><<<grid, block, smem, (ctx)->stream>>>(__VA_ARGS__); \
+      if (st_ == SC_STORE_BF16)                                                                           \
+        KERNEL<kD3Q19, __nv_bfloat16><<<grid, block, smem, (ctx)->stream>>>(__VA_ARGS__);                 \
+      if (st_ == SC_STORE_F64) KERNEL<kD3Q19, double><<<grid, block, smem, (ctx)->stream>>>(__VA_ARGS__); \
+    } else {                                                                                              \
+      if (st_ == SC_STORE_F32) KERNEL<kD2Q9, float><<<grid, block, smem, (ctx)->stream>>>(__VA_ARGS__);   \
+      if (st_ == SC_STORE_F16) KERNEL<kD2Q9, __half><<<grid, block, smem, (ctx)->stream>>>(__VA_ARGS__);  \
+      if (st_ == SC_STORE_BF16)                                                                           \
+        KERNEL<kD2Q9, __nv_bfloat16><<<grid, block, smem, (ctx)->stream>>>(__VA_ARGS__);                  \
+      if (st_ == SC_STORE_F64) KERNEL<kD2Q9, double><<<grid, block, smem, (ctx)->stream>>>(__VA_ARGS__);  \
+    }                                                                                                     \
+  } while (0)
+
+// FP64 density / pseudopotential fields of the current state (cached per step count).
+sc_status ensure_fields(sc_ctx *c) {
+  if (c->fields_at == c->steps) return SC_OK;
+  PopArgs a = pop_args(c, c->cur);
+  SC_POP_DISPATCH(c, fields_kernel, grid_for(c->N, 256), 256, 0, a, c->p.psi_self, fields_of(c));
+  SC_CUDA(cudaGetLastError());
+  c->fields_at = c->steps;
+  return SC_OK;
+}
+
+template <class CT>
+StepArgs<CT> step_args(sc_ctx *c) {
+  StepArgs<CT> a;
+  memset(&a, 0, sizeof(a));
+  a.src = c->ws + c->L.off_pop[c->cur];
+  a.dst = c->ws + c->L.off_pop[1 - c->cur];
+  a.nx = c->p.nx;
+  a.ny = c->p.ny;
+  a.nz = c->p.nz;
+  a.tile_z = c->tile_z;
+  a.N = c->N;
+  const double cs2 = 1.0 / 3.0;
+  for (int J = 0; J < 2; ++J) {
+    a.nbar[J] = CT(c->nbar[J]);
+    a.omega[J] = CT(1.0 / c->p.tau[J]);
+    a.guo[J] = CT(1.0 - 0.5 / c->p.tau[J]);
+    a.gself[J] = CT(-c->p.G_self[J] * cs2);
+    a.psibar[J] = CT(c->psibar[J]);
+    for (int i = 0; i < 19; ++i) {
+      a.scale[J][i] = CT(c->scale[J][i]);
+      a.inv_scale[J][i] = CT(c->inv_scale[J][i]);
+    }
+  }
+  a.gcross = CT(-c->p.G * cs2);
+  a.self_on = (c->p.G_self[0] != 0.0 || c->p.G_self[1] != 0.0) ? 1 : 0;
+  a.psi_exp = c->p.psi_self == SC_PSI_EXP ? 1 : 0;
+  a.err = status_word(c);
+  return a;
+}
+
+sc_status launch_one_step(sc_ctx *c) {
+  StepLaunch l;
+  l.lattice = c->p.lattice == SC_D3Q19 ? kD3Q19 : kD2Q9;
+  l.stencil = c->p.stencil == SC_FORCE_E6 ? kE6 : kE4;
+  l.tile_y = c->tile_y;
+  l.grid = dim3((c->p.nx + 31) / 32, (c->p.ny + c->tile_y - 1) / c->tile_y, (c->p.nz + c->tile_z - 1) / c->tile_z);
+  l.stream = c->stream;
+  cudaError_t e;
+  switch (c->p.storage) {
+    case SC_STORE_F32: e = launch_step_f32(l, step_args<float>(c)); break;
+    case SC_STORE_F16: e = launch_step_f16(l, step_args<float>(c)); break;
+    case SC_STORE_BF16: e = launch_step_bf16(l, step_args<float>(c)); break;
+    default: e = launch_step_f64(l, step_args<double>(c)); break;
+  }
+  if (e != cudaSuccess) return fail(SC_ECUDA, "step kernel launch: %s", cudaGetErrorString(e));
+  c->cur = 1 - c->cur;
+  c->launches++;
+  c->steps++;
+  return SC_OK;
+}
+
+// Deterministic sums / maxima of the two initial fields.
+sc_status init_reductions(sc_ctx *c, const double *nA0, const double *nB0, double *mean, double *maxdev) {
+  const int blocks = grid_for(c->N, 256) < kMaxPartialBlocks ? grid_for(c->N, 256) : kMaxPartialBlocks;
+  double *part = partial_of(c);
+  double *sc = status_scalars(c);
+  min2_partial_kernel<<<blocks, 256, 0, c->stream>>>(nA0, nB0, c->N, part);
+  SC_CUDA(cudaGetLastError());
+  double *mins = (double *)malloc(sizeof(double) * blocks);
+  if (!mins) return fail(SC_ENOMEM, "host allocation failed");
+  cudaError_t e = cudaMemcpyAsync(mins, part, sizeof(double) * blocks, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    free(mins);
+    return fail(SC_ECUDA, "reading initial-field minima: %s", cudaGetErrorString(e));
+  }
+  bool bad = false;
+  for (int k = 0; k < blocks; ++k) bad |= !(mins[k] > 0.0);
+  free(mins);
+  if (bad) return fail(SC_EINVAL, "initial densities must be finite and > 0");
+  sum2_partial_kernel<<<blocks, 256, 0, c->stream>>>(nA0, nB0, c->N, part);
+  totals_finalize_kernel<<<1, 32, 0, c->stream>>>(part, blocks, 2, sc);
+  SC_CUDA(cudaGetLastError());
+  SC_CUDA(cudaMemcpyAsync(mean, sc, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  SC_CUDA(cudaStreamSynchronize(c->stream));
+  mean[0] /= (double)c->N;
+  mean[1] /= (double)c->N;
+  maxdev_partial_kernel<<<blocks, 256, 0, c->stream>>>(nA0, nB0, c->N, mean[0], mean[1], part);
+  SC_CUDA(cudaGetLastError());
+  double *md = (double *)malloc(sizeof(double) * 2 * blocks);
+  if (!md) return fail(SC_ENOMEM, "host allocation failed");
+  e = cudaMemcpyAsync(md, part, sizeof(double) * 2 * blocks, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    free(md);
+    return fail(SC_ECUDA, "reading initial-field deviations: %s", cudaGetErrorString(e));
+  }
+  maxdev[0] = maxdev[1] = 0.0;
+  for (int k = 0; k < blocks; ++k) {
+    maxdev[0] = fmax(maxdev[0], md[2 * k]);
+    maxdev[1] = fmax(maxdev[1], md[2 * k + 1]);
+  }
+  free(md);
+  return SC_OK;
+}
+
+double lattice_w(int lattice, int i) {
+  if (lattice == SC_D3Q19) return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+  return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t sc_workspace_bytes(const sc_params *params) {
+  if (validate(params) != SC_OK) return 0;
+  return layout_of(params).total;
+}
+
+sc_status sc_create(const sc_params *params, const double *nA0, const double *nB0, void *workspace, size_t ws_bytes,
+                    void *stream, sc_ctx **out) {
+  if (!out) return fail(SC_EINVAL, "out is NULL");
+  *out = nullptr;
+  sc_status st = validate(params);
+  if (st != SC_OK) return st;
+  if (!nA0 || !nB0 || !workspace) return fail(SC_EINVAL, "initial fields and workspace must be non-NULL");
+  if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return fail(SC_EINVAL, "workspace must be 256-byte aligned");
+  Layout L = layout_of(params);
+  if (ws_bytes < L.total) return fail(SC_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, L.total);
+  sc_ctx *c = new (std::nothrow) sc_ctx;
+  if (!c) return fail(SC_ENOMEM, "host allocation failed");
+  memset(c, 0, sizeof(*c));
+  c->p = *params;
+  c->N = (int64_t)params->nx * params->ny * params->nz;
+  c->Q = q_of(params);
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->ws = static_cast<char *>(workspace);
+  c->L = L;
+  c->cur = 0;
+  c->tile_y = default_tile_y(params);
+  c->tile_z = default_tile_z(params);
+  c->fields_at = -1;
+  double mean[2], maxdev[2];
+  cudaError_t e = cudaMemsetAsync(c->ws + L.off_status, 0, kStatusBytes, c->stream);
+  if (e != cudaSuccess) {
+    delete c;
+    return fail(SC_ECUDA, "clearing the status word: %s", cudaGetErrorString(e));
+  }
+  st = init_reductions(c, nA0, nB0, mean, maxdev);
+  if (st != SC_OK) {
+    delete c;
+    return st;
+  }
+  for (int J = 0; J < 2; ++J) {
+    c->nbar[J] = mean[J];
+    c->psibar[J] = params->psi_self == SC_PSI_EXP ? exp(-1.0 / mean[J]) : mean[J];
+    for (int i = 0; i < 19; ++i) {
+      double s = 1.0;
+      if (params->storage == SC_STORE_F16 && i < c->Q) {
+        // largest power of two keeping max |g| * s <= 2^11 (FP16 max 65504: x32 headroom)
+        const double m = lattice_w(params->lattice, i) * fmax(maxdev[J], 1e-3);
+        s = ldexp(1.0, (int)floor(log2(2048.0 / m)));
+      }
+      c->scale[J][i] = s;
+      c->inv_scale[J][i] = 1.0 / s;
+    }
+  }
+  PopArgs a = pop_args(c, 0);
+  SC_POP_DISPATCH(c, pop_kernel, grid_for(c->N, 256), 256, 0, a, 0, nA0, nB0, nullptr);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    delete c;
+    return fail(SC_ECUDA, "initialising populations: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return SC_OK;
+}
+
+sc_status sc_step(sc_ctx *c, int64_t nsteps) {
+  if (!c) return fail(SC_EINVAL, "ctx is NULL");
+  if (nsteps < 0) return fail(SC_EINVAL, "nsteps must be >= 0");
+  for (int64_t t = 0; t < nsteps; ++t) {
+    sc_status st = launch_one_step(c);
+    if (st != SC_OK) return st;
+  }
+  return SC_OK;
+}
+
+sc_status sc_moments(sc_ctx *c, double *nA, double *nB, double *u) {
+  if (!c || !nA || !nB) return fail(SC_EINVAL, "ctx, nA and nB must be non-NULL");
+  sc_status st = ensure_fields(c);
+  if (st != SC_OK) return st;
+  double *F = fields_of(c);
+  SC_CUDA(cudaMemcpyAsync(nA, F, sizeof(double) * c->N, cudaMemcpyDeviceToDevice, c->stream));
+  SC_CUDA(cudaMemcpyAsync(nB, F + c->N, sizeof(double) * c->N, cudaMemcpyDeviceToDevice, c->stream));
+  if (u) {
+    PopArgs a = pop_args(c, c->cur);
+    ForceParams fp = force_params(c);
+    const int g = grid_for(c->N, 128);
+    const int lat = c->p.lattice, sten = c->p.stencil, s = c->p.storage;
+#define SC_VEL(LAT, STEN, ST) velocity_kernel<LAT, STEN, ST><<<g, 128, 0, c->stream>>>(a, fp, F, u)
+#define SC_VEL_ST(LAT, STEN)                    \
+  do {                                          \
+    if (s == SC_STORE_F32) SC_VEL(LAT, STEN, float);         \
+    if (s == SC_STORE_F16) SC_VEL(LAT, STEN, __half);        \
+    if (s == SC_STORE_BF16) SC_VEL(LAT, STEN, __nv_bfloat16); \
+    if (s == SC_STORE_F64) SC_VEL(LAT, STEN, double);        \
+  } while (0)
+    if (lat == SC_D3Q19 && sten == SC_FORCE_E4) SC_VEL_ST(kD3Q19, kE4);
+    if (lat == SC_D3Q19 && sten == SC_FORCE_E6) SC_VEL_ST(kD3Q19, kE6);
+    if (lat == SC_D2Q9) SC_VEL_ST(kD2Q9, kE4);
+#undef SC_VEL_ST
+#undef SC_VEL
+    SC_CUDA(cudaGetLastError());
+  }
+  return SC_OK;
+}
+
+sc_status sc_get_populations(sc_ctx *c, double *f) {
+  if (!c || !f) return fail(SC_EINVAL, "ctx and f must be non-NULL");
+  PopArgs a = pop_args(c, c->cur);
+  SC_POP_DISPATCH(c, pop_kernel, grid_for(c->N, 256), 256, 0, a, 2, nullptr, nullptr, f);
+  SC_CUDA(cudaGetLastError());
+  return SC_OK;
+}
+
+sc_status sc_set_populations(sc_ctx *c, const double *f) {
+  if (!c || !f) return fail(SC_EINVAL, "ctx and f must be non-NULL");
+  PopArgs a = pop_args(c, c->cur);
+  SC_POP_DISPATCH(c, pop_kernel, grid_for(c->N, 256), 256, 0, a, 1, nullptr, nullptr, const_cast<double *>(f));
+  SC_CUDA(cudaGetLastError());
+  c->fields_at = -1;
+  return SC_OK;
+}
+
+size_t sc_state_bytes(const sc_ctx *c) { return c ? c->L.pop_bytes : 0; }
+
+sc_status sc_get_state(sc_ctx *c, void *dst, size_t bytes) {
+  if (!c || !dst) return fail(SC_EINVAL, "ctx and dst must be non-NULL");
+  if (bytes != c->L.pop_bytes) return fail(SC_EINVAL, "state is %zu bytes, got %zu", c->L.pop_bytes, bytes);
+  SC_CUDA(cudaMemcpyAsync(dst, c->ws + c->L.off_pop[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
+  return SC_OK;
+}
+
+sc_status sc_set_state(sc_ctx *c, const void *src, size_t bytes) {
+  if (!c || !src) return fail(SC_EINVAL, "ctx and src must be non-NULL");
+  if (bytes != c->L.pop_bytes) return fail(SC_EINVAL, "state is %zu bytes, got %zu", c->L.pop_bytes, bytes);
+  SC_CUDA(cudaMemcpyAsync(c->ws + c->L.off_pop[c->cur], src, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  c->fields_at = -1;
+  return SC_OK;
+}
+
+sc_status sc_pressure_profile(sc_ctx *c, int32_t kind, const double centre[3], double bin_width, int32_t nbins,
+                              double *out) {
+  if (!c || !out || !centre) return fail(SC_EINVAL, "ctx, centre and out must be non-NULL");
+  if (kind < SC_PROFILE_RADIAL || kind > SC_PROFILE_AXIS_X) return fail(SC_EINVAL, "unknown profile kind %d", kind);
+  if (nbins < 1 || nbins > 4096) return fail(SC_EINVAL, "nbins must be in [1, 4096]");
+  if (kind == SC_PROFILE_RADIAL && !(bin_width > 0.0)) return fail(SC_EINVAL, "bin_width must be > 0");
+  for (int m = 0; m < 3; ++m)
+    if (!isfinite(centre[m])) return fail(SC_EINVAL, "centre must be finite");
+  sc_status st = ensure_fields(c);
+  if (st != SC_OK) return st;
+  ProfileArgs pa;
+  pa.kind = kind;
+  for (int m = 0; m < 3; ++m) pa.centre[m] = centre[m];
+  pa.bin_width = bin_width;
+  pa.nbins = nbins;
+  pa.dim = (c->p.lattice == SC_D3Q19 && c->p.nz > 1) ? 3 : 2;
+  const size_t row_bytes = (size_t)nbins * 6 * sizeof(double);
+  int64_t blocks = (int64_t)(kPartialBytes / row_bytes);
+  if (blocks > kMaxPartialBlocks) blocks = kMaxPartialBlocks;
+  if (blocks > (c->N + 31) / 32) blocks = (c->N + 31) / 32;
+  if (blocks < 1) blocks = 1;
+  pa.chunk = (c->N + blocks - 1) / blocks;
+  pa.chunk = (pa.chunk + 31) / 32 * 32;
+  blocks = (c->N + pa.chunk - 1) / pa.chunk;
+  ForceParams fp = force_params(c);
+  const int lat = c->p.lattice, sten = c->p.stencil;
+  if (lat == SC_D3Q19 && sten == SC_FORCE_E4) {
+    SC_CUDA(cudaFuncSetAttribute(profile_partial_kernel<kD3Q19, kE4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)row_bytes));
+    profile_partial_kernel<kD3Q19, kE4><<<(int)blocks, 32, row_bytes, c->stream>>>(fp, pa, fields_of(c), partial_of(c));
+  } else if (lat == SC_D3Q19) {
+    SC_CUDA(cudaFuncSetAttribute(profile_partial_kernel<kD3Q19, kE6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)row_bytes));
+    profile_partial_kernel<kD3Q19, kE6><<<(int)blocks, 32, row_bytes, c->stream>>>(fp, pa, fields_of(c), partial_of(c));
+  } else {
+    SC_CUDA(cudaFuncSetAttribute(profile_partial_kernel<kD2Q9, kE4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)row_bytes));
+    profile_partial_kernel<kD2Q9, kE4><<<(int)blocks, 32, row_bytes, c->stream>>>(fp, pa, fields_of(c), partial_of(c));
+  }
+  SC_CUDA(cudaGetLastError());
+  profile_finalize_kernel<<<(nbins + 127) / 128, 128, 0, c->stream>>>(partial_of(c), (int)blocks, nbins, out);
+  SC_CUDA(cudaGetLastError());
+  return SC_OK;
+}
+
+sc_status sc_bulk_pressure_at(sc_ctx *c, const int32_t node[3], double *out) {
+  if (!c || !node || !out) return fail(SC_EINVAL, "ctx, node and out must be non-NULL");
+  const int nn[3] = {c->p.nx, c->p.ny, c->p.nz};
+  for (int m = 0; m < 3; ++m)
+    if (node[m] < 0 || node[m] >= nn[m]) return fail(SC_EINVAL, "node outside the lattice");
+  sc_status st = ensure_fields(c);
+  if (st != SC_OK) return st;
+  const int64_t s = (int64_t)node[0] + (int64_t)c->p.nx * (node[1] + (int64_t)c->p.ny * node[2]);
+  bulk_pressure_kernel<<<1, 32, 0, c->stream>>>(force_params(c), fields_of(c), s, out);
+  SC_CUDA(cudaGetLastError());
+  return SC_OK;
+}
+
+sc_status sc_sigma_minimum(const double *rows, int32_t nbins, const double *P_in_out, int32_t dim, double R_lo,
+                           double R_hi, double R_step, double *out, void *stream) {
+  if (!rows || !P_in_out || !out) return fail(SC_EINVAL, "rows, P_in_out and out must be non-NULL");
+  if (nbins < 2) return fail(SC_EINVAL, "need at least two profile rows");
+  if (dim != 2 && dim != 3) return fail(SC_EINVAL, "dim must be 2 or 3");
+  if (!(R_lo > 0.0) || !(R_hi > R_lo) || !(R_step > 0.0) || (R_hi - R_lo) / R_step > 1e7)
+    return fail(SC_EINVAL, "need 0 < R_lo < R_hi, R_step > 0 and at most 1e7 grid points");
+  sigma_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(rows, nbins, P_in_out, dim, R_lo, R_hi, R_step, out);
+  SC_CUDA(cudaGetLastError());
+  return SC_OK;
+}
+
+sc_status sc_totals(sc_ctx *c, double *out) {
+  if (!c || !out) return fail(SC_EINVAL, "ctx and out must be non-NULL");
+  const int blocks = grid_for(c->N, 256) < kMaxPartialBlocks ? grid_for(c->N, 256) : kMaxPartialBlocks;
+  PopArgs a = pop_args(c, c->cur);
+  SC_POP_DISPATCH(c, totals_partial_kernel, blocks, 256, 0, a, partial_of(c));
+  totals_finalize_kernel<<<1, 32, 0, c->stream>>>(partial_of(c), blocks, 5, out);
+  SC_CUDA(cudaGetLastError());
+  return SC_OK;
+}
+
+sc_status sc_sync(sc_ctx *c) {
+  if (!c) return fail(SC_EINVAL, "ctx is NULL");
+  SC_CUDA(cudaStreamSynchronize(c->stream));
+  unsigned int w = 0;
+  SC_CUDA(cudaMemcpy(&w, status_word(c), sizeof(w), cudaMemcpyDeviceToHost));
+  if (w) {
+    SC_CUDA(cudaMemset(status_word(c), 0, sizeof(unsigned int)));
+    return fail(SC_ENAN, "a time step met a non-positive or non-finite density (status 0x%x)", w);
+  }
+  return SC_OK;
+}
+
+sc_status sc_run_host(const sc_params *params, const double *nA0, const double *nB0, int64_t nsteps, double *nA,
+                      double *nB, void *workspace, size_t ws_bytes, void *stream) {
+  sc_status st = validate(params);
+  if (st != SC_OK) return st;
+  if (!nA0 || !nB0 || !nA || !nB || !workspace) return fail(SC_EINVAL, "buffers must be non-NULL");
+  if (nsteps < 0) return fail(SC_EINVAL, "nsteps must be >= 0");
+  Layout L = layout_of(params);
+  if (ws_bytes < L.total) return fail(SC_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, L.total);
+  const int64_t N = (int64_t)params->nx * params->ny * params->nz;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // stage the initial fields in the (not yet used) FP64 field region
+  double *stage = reinterpret_cast<double *>(static_cast<char *>(workspace) + L.off_fields);
+  SC_CUDA(cudaMemcpyAsync(stage, nA0, sizeof(double) * N, cudaMemcpyHostToDevice, s));
+  SC_CUDA(cudaMemcpyAsync(stage + N, nB0, sizeof(double) * N, cudaMemcpyHostToDevice, s));
+  sc_ctx *c = nullptr;
+  st = sc_create(params, stage, stage + N, workspace, ws_bytes, stream, &c);
+  if (st != SC_OK) return st;
+  st = sc_step(c, nsteps);
+  if (st == SC_OK) st = ensure_fields(c);
+  if (st == SC_OK) {
+    cudaError_t e = cudaMemcpyAsync(nA, fields_of(c), sizeof(double) * N, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(nB, fields_of(c) + N, sizeof(double) * N, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) st = fail(SC_ECUDA, "copying densities to the host: %s", cudaGetErrorString(e));
+  }
+  if (st == SC_OK) st = sc_sync(c);
+  sc_destroy(c);
+  return st;
+}
+
+int64_t sc_kernel_launches(const sc_ctx *c) { return c ? c->launches : 0; }
+
+sc_status sc_reference_density(const sc_ctx *c, double nbar[2]) {
+  if (!c || !nbar) return fail(SC_EINVAL, "ctx and nbar must be non-NULL");
+  nbar[0] = c->nbar[0];
+  nbar[1] = c->nbar[1];
+  return SC_OK;
+}
+
+void sc_destroy(sc_ctx *c) { delete c; }
+
+const char *sc_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

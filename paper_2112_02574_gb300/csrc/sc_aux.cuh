@@ -1,0 +1,511 @@
+// Kernels around the time step: initial state, population access, FP64
+// density / pseudopotential fields, the common velocity, the lattice pressure
+// tensor with its profiles, the sigma[R] minimum and conserved totals.
+// All analysis arithmetic is FP64 (arXiv:2112.02574, sections 2 and 3).
+#pragma once
+
+#include "sc_common.cuh"
+
+namespace scgb {
+
+// Storage read / write in FP64 (natural populations f = g / scale + w nbar).
+template <class ST>
+__device__ __forceinline__ double load_dev(const ST *p, double inv_scale) {
+  return double(Codec<ST, float>::load(p, 1.0f)) * inv_scale;
+}
+template <>
+__device__ __forceinline__ double load_dev<double>(const double *p, double inv_scale) {
+  return __ldg(p) * inv_scale;
+}
+template <class ST>
+__device__ __forceinline__ void store_dev(ST *p, double v, double scale) {
+  Codec<ST, float>::store(p, float(v * scale), 1.0f);
+}
+template <>
+__device__ __forceinline__ void store_dev<double>(double *p, double v, double scale) {
+  *p = v * scale;
+}
+
+struct PopArgs {
+  void *buf;         // stored populations [2][Q][N]
+  int nx, ny, nz;
+  int64_t N;
+  double nbar[2];
+  double scale[2][19];
+  double inv_scale[2][19];
+};
+
+__device__ __forceinline__ void coords(int64_t s, int nx, int ny, int &x, int &y, int &z) {
+  x = int(s % nx);
+  const int64_t r = s / nx;
+  y = int(r % ny);
+  z = int(r / ny);
+}
+__device__ __forceinline__ int64_t site_at(int x, int y, int z, int nx, int ny, int nz) {
+  x = ((x % nx) + nx) % nx;
+  y = ((y % ny) + ny) % ny;
+  z = ((z % nz) + nz) % nz;
+  return (int64_t)x + (int64_t)nx * (y + (int64_t)ny * z);
+}
+
+// mode 0: initial rest equilibrium from densities n0 (FP64 [2][N]):
+//         buf[J][i][y] = encode(w_i (n0_J(y + xi_i) - nbar_J)), so that the
+//         first pull delivers f_i(x) = w_i n0_J(x);
+// mode 1: natural populations f (FP64 [2][Q][N]) -> storage (inverse pull);
+// mode 2: storage -> natural populations f.
+template <int LAT, class ST>
+__global__ void pop_kernel(PopArgs a, int mode, const double *n0A, const double *n0B, double *f) {
+  using L = Lattice<LAT>;
+  ST *buf = static_cast<ST *>(a.buf);
+  const int64_t N = a.N;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+    int x, y, z;
+    coords(s, a.nx, a.ny, x, y, z);
+#pragma unroll
+    for (int J = 0; J < 2; ++J) {
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+        const double w = L::w(i);
+        const int64_t fwd = site_at(x + cx, y + cy, z + cz, a.nx, a.ny, a.nz);
+        const int64_t bwd = site_at(x - cx, y - cy, z - cz, a.nx, a.ny, a.nz);
+        ST *slot = buf + ((int64_t)J * L::Q + i) * N;
+        if (mode == 0) {
+          const double n = (J == 0 ? n0A : n0B)[fwd];
+          store_dev<ST>(slot + s, w * (n - a.nbar[J]), a.scale[J][i]);
+        } else if (mode == 1) {
+          const double fv = f[((int64_t)J * L::Q + i) * N + fwd];
+          store_dev<ST>(slot + s, fv - w * a.nbar[J], a.scale[J][i]);
+        } else {
+          f[((int64_t)J * L::Q + i) * N + s] = load_dev<ST>(slot + bwd, a.inv_scale[J][i]) + w * a.nbar[J];
+        }
+      }
+    }
+  }
+}
+
+// FP64 density fields n_J (and psi_J) from the stored state (pull + sum).
+// fields: [4][N] = n_A, n_B, psi_A, psi_B.
+template <int LAT, class ST>
+__global__ void fields_kernel(PopArgs a, int psi_exp, double *fields) {
+  using L = Lattice<LAT>;
+  const ST *buf = static_cast<const ST *>(a.buf);
+  const int64_t N = a.N;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+    int x, y, z;
+    coords(s, a.nx, a.ny, x, y, z);
+#pragma unroll
+    for (int J = 0; J < 2; ++J) {
+      double dn = 0.0;
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        const int64_t bwd = site_at(x - L::c(i, 0), y - L::c(i, 1), z - L::c(i, 2), a.nx, a.ny, a.nz);
+        dn += load_dev<ST>(buf + ((int64_t)J * L::Q + i) * N + bwd, a.inv_scale[J][i]);
+      }
+      const double n = a.nbar[J] + dn;
+      fields[J * N + s] = n;
+      fields[(2 + J) * N + s] = psi_exp ? exp(-1.0 / n) : n;
+    }
+  }
+}
+
+struct ForceParams {
+  double G, G_self[2];
+  int nx, ny, nz;
+  int64_t N;
+};
+
+// Eq. sc_force at site s from FP64 fields, +/- pairs first.
+template <int LAT, int STEN>
+__device__ __forceinline__ void force64(const ForceParams &p, const double *fields, int x, int y, int z, int64_t s,
+                                        double F[2][3]) {
+  using SN = Stencil<LAT, STEN>;
+  const double cs2 = 1.0 / 3.0;
+  double S[2][3] = {{0, 0, 0}, {0, 0, 0}}, T[2][3] = {{0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+  for (int k = 0; k < SN::NH; ++k) {
+    const int v0 = SN::v(k, 0), v1 = SN::v(k, 1), v2 = SN::v(k, 2);
+    const int64_t sp = site_at(x + v0, y + v1, z + v2, p.nx, p.ny, p.nz);
+    const int64_t sm = site_at(x - v0, y - v1, z - v2, p.nx, p.ny, p.nz);
+    const double W = SN::W(k);
+    const int v[3] = {v0, v1, v2};
+#pragma unroll
+    for (int J = 0; J < 2; ++J) {
+      const double d = fields[J * p.N + sp] - fields[J * p.N + sm];
+      const double e = fields[(2 + J) * p.N + sp] - fields[(2 + J) * p.N + sm];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        S[J][m] += W * v[m] * d;
+        T[J][m] += W * v[m] * e;
+      }
+    }
+  }
+#pragma unroll
+  for (int J = 0; J < 2; ++J)
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+      F[J][m] = -p.G * cs2 * fields[J * p.N + s] * S[1 - J][m] -
+                p.G_self[J] * cs2 * fields[(2 + J) * p.N + s] * T[J][m];
+}
+
+// Common velocity of Eq. u (force included), FP64 [3][N].
+template <int LAT, int STEN, class ST>
+__global__ void velocity_kernel(PopArgs a, ForceParams fp, const double *fields, double *u) {
+  using L = Lattice<LAT>;
+  const ST *buf = static_cast<const ST *>(a.buf);
+  const int64_t N = a.N;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+    int x, y, z;
+    coords(s, a.nx, a.ny, x, y, z);
+    double F[2][3];
+    force64<LAT, STEN>(fp, fields, x, y, z, s, F);
+    double j[2][3] = {{0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+    for (int J = 0; J < 2; ++J)
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        const int64_t bwd = site_at(x - L::c(i, 0), y - L::c(i, 1), z - L::c(i, 2), a.nx, a.ny, a.nz);
+        const double g = load_dev<ST>(buf + ((int64_t)J * L::Q + i) * N + bwd, a.inv_scale[J][i]);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) j[J][m] += L::c(i, m) * g;
+      }
+    const double n = fields[s] + fields[N + s];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) u[m * N + s] = ((j[0][m] + 0.5 * F[0][m]) + (j[1][m] + 0.5 * F[1][m])) / n;
+  }
+}
+
+// Lattice pressure tensor of Eq. sm:pt at one site; P = {xx, yy, zz, xy, xz, yz}.
+template <int LAT, int STEN>
+__device__ __forceinline__ void ptensor64(const ForceParams &p, const double *fields, int x, int y, int z, int64_t s,
+                                          double P[6]) {
+  using SN = Stencil<LAT, STEN>;
+  const double cs2 = 1.0 / 3.0;
+  constexpr int MU[6] = {0, 1, 2, 0, 0, 1}, NU[6] = {0, 1, 2, 1, 2, 2};
+  double C[4][6];
+#pragma unroll
+  for (int f = 0; f < 4; ++f)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) C[f][c] = 0.0;
+#pragma unroll
+  for (int k = 0; k < SN::NH; ++k) {
+    const int v[3] = {SN::v(k, 0), SN::v(k, 1), SN::v(k, 2)};
+    const int64_t sp = site_at(x + v[0], y + v[1], z + v[2], p.nx, p.ny, p.nz);
+    const int64_t sm = site_at(x - v[0], y - v[1], z - v[2], p.nx, p.ny, p.nz);
+    const double W = SN::W(k);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const double sum = fields[f * p.N + sp] + fields[f * p.N + sm];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        const int vv = v[MU[c]] * v[NU[c]];
+        if (vv) C[f][c] += W * vv * sum;
+      }
+    }
+  }
+  const double nA = fields[s], nB = fields[p.N + s], psA = fields[2 * p.N + s], psB = fields[3 * p.N + s];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const double ideal = c < 3 ? (nA + nB) * cs2 : 0.0;
+    P[c] = ideal + 0.5 * p.G * cs2 * nA * C[1][c] + 0.5 * p.G * cs2 * nB * C[0][c] +
+           0.5 * p.G_self[0] * cs2 * psA * C[2][c] + 0.5 * p.G_self[1] * cs2 * psB * C[3][c];
+  }
+}
+
+struct ProfileArgs {
+  int kind;  // sc_profile_kind
+  double centre[3];
+  double bin_width;
+  int nbins;
+  int dim;   // 2 or 3
+  int64_t chunk;  // sites per block
+};
+
+// Per-block partial sums of a profile: one warp per block accumulates into its
+// own shared-memory bins, lane by lane in a fixed order (deterministic), then
+// writes rows [nbins][6] = (sum coordinate, sum P_N, sum P_T, sum n_A, sum n_B, count).
+template <int LAT, int STEN>
+__global__ void __launch_bounds__(32) profile_partial_kernel(ForceParams fp, ProfileArgs pa, const double *fields,
+                                                             double *partial) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double *bins = reinterpret_cast<double *>(smem_raw);
+  const int lane = threadIdx.x;
+  for (int k = lane; k < pa.nbins * 6; k += 32) bins[k] = 0.0;
+  __syncwarp();
+  const int64_t N = fp.N;
+  const int64_t s0 = blockIdx.x * pa.chunk, s1 = min(N, s0 + pa.chunk);
+  const int cx = int(floor(pa.centre[0] + 0.5)), cy = int(floor(pa.centre[1] + 0.5)),
+            cz = int(floor(pa.centre[2] + 0.5));
+  for (int64_t base = s0; base < s1; base += 32) {
+    const int64_t s = base + lane;
+    int bin = -1;
+    double vals[5] = {0, 0, 0, 0, 0};
+    if (s < s1) {
+      int x, y, z;
+      coords(s, fp.nx, fp.ny, x, y, z);
+      double coord = 0.0, d[3] = {0, 0, 0};
+      if (pa.kind == SC_PROFILE_RADIAL) {
+        const int c[3] = {x, y, z}, L[3] = {fp.nx, fp.ny, fp.nz};
+        double r2 = 0.0;
+        for (int m = 0; m < 3; ++m) {
+          double dd = c[m] - pa.centre[m];
+          dd -= L[m] * floor(dd / L[m] + 0.5);  // minimum image
+          d[m] = dd;
+          r2 += dd * dd;
+        }
+        coord = sqrt(r2);
+        bin = int(floor(coord / pa.bin_width));
+      } else if (pa.kind == SC_PROFILE_PLANAR_Z) {
+        coord = z;
+        bin = z;
+      } else {
+        const int k = ((x - cx) % fp.nx + fp.nx) % fp.nx;
+        if (y == ((cy % fp.ny) + fp.ny) % fp.ny && z == ((cz % fp.nz) + fp.nz) % fp.nz) {
+          coord = k;
+          bin = k;
+        }
+      }
+      if (bin >= pa.nbins) bin = -1;
+      if (bin >= 0) {
+        double P[6];
+        ptensor64<LAT, STEN>(fp, fields, x, y, z, s, P);
+        double PN, PT;
+        if (pa.kind == SC_PROFILE_RADIAL) {
+          const double tr = pa.dim == 3 ? P[0] + P[1] + P[2] : P[0] + P[1];
+          if (coord == 0.0) {
+            PN = PT = tr / pa.dim;
+          } else {
+            const double e[3] = {d[0] / coord, d[1] / coord, d[2] / coord};
+            PN = e[0] * e[0] * P[0] + e[1] * e[1] * P[1] + e[2] * e[2] * P[2] + 2.0 * e[0] * e[1] * P[3] +
+                 2.0 * e[0] * e[2] * P[4] + 2.0 * e[1] * e[2] * P[5];
+            PT = (tr - PN) / (pa.dim - 1);
+          }
+        } else if (pa.kind == SC_PROFILE_PLANAR_Z) {
+          PN = P[2];
+          PT = 0.5 * (P[0] + P[1]);
+        } else {
+          PN = P[0];
+          PT = P[1];
+        }
+        vals[0] = coord;
+        vals[1] = PN;
+        vals[2] = PT;
+        vals[3] = fields[s];
+        vals[4] = fields[N + s];
+      }
+    }
+    // fixed-order accumulation: lane l's contribution is added in iteration l
+    for (int l = 0; l < 32; ++l) {
+      const int b = __shfl_sync(0xffffffffu, bin, l);
+      double v = 0.0;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        const double t = __shfl_sync(0xffffffffu, vals[c], l);
+        if (lane == c) v = t;
+      }
+      if (b >= 0 && lane < 6) bins[b * 6 + lane] += (lane == 5) ? 1.0 : v;
+      __syncwarp();
+    }
+  }
+  __syncwarp();
+  double *out = partial + (int64_t)blockIdx.x * pa.nbins * 6;
+  for (int k = lane; k < pa.nbins * 6; k += 32) out[k] = bins[k];
+}
+
+// Sum the per-block partials in block order and turn sums into means.
+__global__ void profile_finalize_kernel(const double *partial, int nblocks, int nbins, double *out) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbins; b += gridDim.x * blockDim.x) {
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < nblocks; ++k)
+#pragma unroll
+      for (int c = 0; c < 6; ++c) acc[c] += partial[((int64_t)k * nbins + b) * 6 + c];
+    const double cnt = acc[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) out[b * 6 + c] = cnt > 0 ? acc[c] / cnt : 0.0;
+    out[b * 6 + 5] = cnt;
+  }
+}
+
+// Bulk pressure of Eq. bulkp (e_2 = 1) at one node.
+__global__ void bulk_pressure_kernel(ForceParams fp, const double *fields, int64_t s, double *out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double cs2 = 1.0 / 3.0;
+  const double nA = fields[s], nB = fields[fp.N + s], psA = fields[2 * fp.N + s], psB = fields[3 * fp.N + s];
+  out[0] = (nA + nB) * cs2 + fp.G * cs2 * nA * nB + 0.5 * fp.G_self[0] * cs2 * psA * psA +
+           0.5 * fp.G_self[1] * cs2 * psB * psB;
+}
+
+// sigma[R] minimum (section 3) on one warp; see sc_sigma_minimum in sc.h.
+__global__ void __launch_bounds__(32) sigma_kernel(const double *rows, int nbins, const double *pio, int dim,
+                                                   double R_lo, double R_hi, double R_step, double *out) {
+  const int lane = threadIdx.x;
+  __shared__ double s_C;
+  if (lane == 0) {
+    // trapezoid of r^(dim-1) P_T over the non-empty rows, in order
+    double T = 0.0, rp = 0.0, fp = 0.0, rmax = 0.0;
+    bool first = true;
+    for (int b = 0; b < nbins; ++b) {
+      if (rows[b * 6 + 5] <= 0.0) continue;
+      const double r = rows[b * 6 + 0], pt = rows[b * 6 + 2];
+      const double f = (dim == 3 ? r * r : r) * pt;
+      if (!first) T += 0.5 * (f + fp) * (r - rp);
+      first = false;
+      rp = r;
+      fp = f;
+      rmax = r;
+    }
+    const double Pout = pio[1];
+    s_C = Pout * (dim == 3 ? rmax * rmax * rmax / 3.0 : rmax * rmax / 2.0) - T;
+  }
+  __syncwarp();
+  const double Pin = pio[0], Pout = pio[1], dP = Pin - Pout, C = s_C;
+  auto sigma = [&](double R) { return dim == 3 ? dP * R / 3.0 + C / (R * R) : dP * R / 2.0 + C / R; };
+  // grid search: each lane scans a strided subset, then a warp argmin (lowest index on ties)
+  const int ng = int(floor((R_hi - R_lo) / R_step + 0.5)) + 1;
+  double best = INFINITY;
+  int bi = -1;
+  for (int k = lane; k < ng; k += 32) {
+    const double v = sigma(R_lo + k * R_step);
+    if (v < best) {
+      best = v;
+      bi = k;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ob = __shfl_down_sync(0xffffffffu, best, off);
+    const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+    if (oi >= 0 && (ob < best || (ob == best && (bi < 0 || oi < bi)))) {
+      best = ob;
+      bi = oi;
+    }
+  }
+  if (lane == 0) {
+    const double Rs = dim == 3 ? cbrt(6.0 * C / dP) : sqrt(2.0 * C / dP);
+    out[0] = dP;
+    out[1] = C;
+    out[2] = Rs;
+    out[3] = dim == 3 ? 0.5 * dP * Rs : dP * Rs;
+    int k = bi < 1 ? 1 : (bi > ng - 2 ? ng - 2 : bi);
+    double Rg = NAN, sg = NAN;
+    if (ng >= 3) {
+      const double y0 = sigma(R_lo + (k - 1) * R_step), y1 = sigma(R_lo + k * R_step),
+                   y2 = sigma(R_lo + (k + 1) * R_step);
+      const double den = y0 - 2.0 * y1 + y2;
+      const double off = den != 0.0 ? 0.5 * (y0 - y2) / den : 0.0;
+      Rg = R_lo + (k + off) * R_step;
+      sg = y1 - 0.25 * (y0 - y2) * off;
+    }
+    out[4] = Rg;
+    out[5] = sg;
+    out[6] = Pin;
+    out[7] = Pout;
+  }
+}
+
+// Deterministic FP64 totals: per-block partial sums (fixed grid-stride order,
+// fixed tree) of mass_A, mass_B and momentum; finalised in block order.
+template <int LAT, class ST>
+__global__ void __launch_bounds__(256) totals_partial_kernel(PopArgs a, double *partial) {
+  using L = Lattice<LAT>;
+  const ST *buf = static_cast<const ST *>(a.buf);
+  const int64_t N = a.N;
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int J = 0; J < 2; ++J)
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        // stored at the collision site: sums over all sites need no pull
+        const double f = load_dev<ST>(buf + ((int64_t)J * L::Q + i) * N + s, a.inv_scale[J][i]) + L::w(i) * a.nbar[J];
+        acc[J] += f;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) acc[2 + m] += L::c(i, m) * f;
+      }
+  }
+  __shared__ double red[5][256];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) red[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 5) partial[blockIdx.x * 5 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void totals_finalize_kernel(const double *partial, int nblocks, int ncomp, double *out) {
+  const int c = threadIdx.x;
+  if (c >= ncomp) return;
+  double acc = 0.0;
+  for (int k = 0; k < nblocks; ++k) acc += partial[k * ncomp + c];
+  out[c] = acc;
+}
+
+// Deterministic FP64 sums of two fields (used for the mean initial densities).
+__global__ void __launch_bounds__(256) sum2_partial_kernel(const double *a, const double *b, int64_t N,
+                                                           double *partial) {
+  double acc[2] = {0, 0};
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+    acc[0] += a[s];
+    acc[1] += b[s];
+  }
+  __shared__ double red[2][256];
+  red[0][threadIdx.x] = acc[0];
+  red[1][threadIdx.x] = acc[1];
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + w];
+      red[1][threadIdx.x] += red[1][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 2) partial[blockIdx.x * 2 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// max |n_J - nbar_J| of both init fields (for the F16/BF16 scales); one value per block.
+__global__ void __launch_bounds__(256) maxdev_partial_kernel(const double *a, const double *b, int64_t N,
+                                                             double nbarA, double nbarB, double *partial) {
+  double m[2] = {0, 0};
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+    m[0] = fmax(m[0], fabs(a[s] - nbarA));
+    m[1] = fmax(m[1], fabs(b[s] - nbarB));
+  }
+  __shared__ double red[2][256];
+  red[0][threadIdx.x] = m[0];
+  red[1][threadIdx.x] = m[1];
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      red[0][threadIdx.x] = fmax(red[0][threadIdx.x], red[0][threadIdx.x + w]);
+      red[1][threadIdx.x] = fmax(red[1][threadIdx.x], red[1][threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 2) partial[blockIdx.x * 2 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// min of (n_A, n_B) over both init fields, per block (validation: densities > 0).
+__global__ void __launch_bounds__(256) min2_partial_kernel(const double *a, const double *b, int64_t N,
+                                                           double *partial) {
+  double m = INFINITY;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x)
+    m = fmin(m, fmin(a[s], b[s]));  // NaN-propagation: fmin ignores NaN, so flag it explicitly
+  __shared__ double red[256];
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x)
+    if (!(a[s] > 0.0) || !(b[s] > 0.0) || !isfinite(a[s]) || !isfinite(b[s])) bad = 1;
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmin(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = bad ? -1.0 : red[0];
+}
+
+}  // namespace scgb

@@ -1,0 +1,25 @@
+// Host-side entry points of the per-storage kernel instantiation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "sc_common.cuh"
+
+namespace scgb {
+
+struct StepLaunch {
+  int lattice;  // kD2Q9 / kD3Q19
+  int stencil;  // kE4 / kE6
+  int tile_y;   // 1, 2, 4 or 8
+  dim3 grid;
+  cudaStream_t stream;
+};
+
+// Launch one fused time step; returns the launch error (cudaErrorInvalidValue
+// for an unsupported lattice / stencil / tile combination).
+cudaError_t launch_step_f32(const StepLaunch &l, const StepArgs<float> &a);
+cudaError_t launch_step_f16(const StepLaunch &l, const StepArgs<float> &a);
+cudaError_t launch_step_bf16(const StepLaunch &l, const StepArgs<float> &a);
+cudaError_t launch_step_f64(const StepLaunch &l, const StepArgs<double> &a);
+
+}  // namespace scgb

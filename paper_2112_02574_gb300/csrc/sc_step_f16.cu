@@ -1,0 +1,3 @@
+// Step-kernel instantiations: FP16 scaled deviation storage, FP32 collision.
+#include "sc_step_inst.cuh"
+cudaError_t scgb::launch_step_f16(const StepLaunch &l, const StepArgs<float> &a) { return launch_any<__half, float>(l, a); }

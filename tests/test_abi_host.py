@@ -1,0 +1,71 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every function include/sc.h declares, and rejects invalid arguments with
+SC_EINVAL before touching any device memory."""
+import ctypes
+
+import pytest
+
+
+@pytest.fixture(scope="module")
+def B():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2112_02574_gb300 import binding
+
+    return binding
+
+
+def test_every_declared_symbol_is_exported(B):
+    names = B.declared_symbols()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(B.lib, n), n
+        assert hasattr(B, n), f"binding lacks {n}"
+
+
+def test_workspace_bytes_layout(B):
+    p = B.make_params((128, 128, 128), storage=B.SC_STORE_F32)
+    ws = B.sc_workspace_bytes(p)
+    pops = 2 * 2 * 19 * 128**3 * 4
+    assert ws >= pops + 4 * 8 * 128**3
+    assert ws % 256 == 0
+    p16 = B.make_params((128, 128, 128), storage=B.SC_STORE_F16)
+    assert B.sc_workspace_bytes(p16) < ws
+
+
+@pytest.mark.parametrize("bad", [
+    dict(shape=(0, 4, 4)),
+    dict(shape=(4, 4, 4), lattice=7),
+    dict(shape=(4, 4, 2), lattice=0),            # D2Q9 with nz != 1
+    dict(shape=(4, 4, 1), lattice=0, stencil=1),  # E6 on D2Q9
+    dict(shape=(4, 4, 4), tau=(0.5, 1.0)),
+    dict(shape=(4, 4, 4), tau=(1.0, float("nan"))),
+    dict(shape=(4, 4, 4), storage=9),
+    dict(shape=(4, 4, 4), tile_y=3),
+    dict(shape=(4, 4, 4), G=float("inf")),
+])
+def test_invalid_parameters_rejected(B, bad):
+    shape = bad.pop("shape")
+    p = B.make_params(shape, **bad)
+    assert B.sc_workspace_bytes(p) == 0
+    assert B.sc_last_error() != ""
+    ctx = ctypes.c_void_p()
+    dummy = ctypes.c_void_p(256)
+    st = B.lib.sc_create(ctypes.byref(p), dummy, dummy, dummy, 1 << 30, None, ctypes.byref(ctx))
+    assert st == B.SC_EINVAL
+    assert not ctx.value
+
+
+def test_null_and_range_arguments(B):
+    assert B.lib.sc_step(None, 1) == B.SC_EINVAL
+    assert B.lib.sc_sync(None) == B.SC_EINVAL
+    assert B.lib.sc_sigma_minimum(None, 10, None, 3, 1.0, 2.0, 0.1, None, None) == B.SC_EINVAL
+    p = B.make_params((8, 8, 8))
+    ctx = ctypes.c_void_p()
+    dummy = ctypes.c_void_p(256)
+    # workspace too small -> SC_ENOMEM before any device work
+    assert B.lib.sc_create(ctypes.byref(p), dummy, dummy, dummy, 16, None, ctypes.byref(ctx)) == B.SC_ENOMEM
+    # misaligned workspace
+    assert B.lib.sc_create(ctypes.byref(p), dummy, dummy, ctypes.c_void_p(257), 1 << 30, None,
+                           ctypes.byref(ctx)) == B.SC_EINVAL

@@ -1,0 +1,259 @@
+"""GPU parity: the fused CUDA step and the analysis kernels, called through the
+C ABI, against the FP64 CPU oracle on the same seeded inputs.
+
+Tolerances
+* FP64 storage + FP64 collision: the same arithmetic as the oracle in another
+  order -> max |f_gpu - f_orc| <= 1e-13 max |f| after the steps run here.
+* FP32 storage (deviations from the rest equilibrium) + FP32 collision: within
+  1e-6 relative of the FP64 oracle (max-norm of each field, normalised by the
+  field's max), the bound the method's FP32 mode is held to.
+* Integer-like results (counts, bitwise symmetries, tile independence in FP64,
+  checkpoint/resume) are exact."""
+import numpy as np
+import pytest
+
+import oracle
+import sc_synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2112_02574_gb300 import binding
+
+    return binding
+
+
+def setup(B, shape, storage, lattice=1, stencil=0, psi=1, tau=(1.0, 0.9), G=2.5, G_self=(-0.4, 0.0), amp=1e-3,
+          radius=None, tile_y=0, tile_z=0, n_in=0.85, n_out=0.15, seed=S.DEFAULT_SEED):
+    nx, ny, nz = shape
+    centre = (nx // 2, ny // 2, nz // 2)
+    R = radius if radius is not None else min(nx, ny, nz if nz > 1 else ny) / 4
+    nA0, nB0 = S.droplet(shape[::-1], centre, R, n_in=n_in, n_out=n_out, amplitude=amp, seed=seed)
+    p = B.make_params(shape, lattice=lattice, stencil=stencil, psi_self=psi, storage=storage, tau=tau, G=G,
+                      G_self=G_self, tile_y=tile_y, tile_z=tile_z)
+    op = oracle.Params(shape=shape, lattice=lattice, stencil=stencil, psi_self=psi, tau=tau, G=G, G_self=G_self)
+    return B.Simulation(p, nA0, nB0), op, nA0, nB0
+
+
+def rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+
+
+CASES = [
+    # (shape, lattice, stencil, psi, G_self) -- every shape spans >1 tile in x and y with a ragged tail
+    ((37, 11, 19), 1, 0, 1, (-0.4, 0.0)),
+    ((70, 9, 6), 1, 0, 0, (0.0, 0.0)),
+    ((35, 10, 18), 1, 1, 1, (-0.4, 0.2)),
+    ((70, 45, 1), 0, 0, 0, (0.0, 0.0)),
+    ((33, 13, 1), 0, 0, 1, (-0.3, 0.0)),
+]
+
+
+@pytest.mark.parametrize("shape,lattice,stencil,psi,G_self", CASES)
+def test_fp64_step_matches_oracle(B, shape, lattice, stencil, psi, G_self):
+    sim, op, nA0, nB0 = setup(B, shape, B.SC_STORE_F64, lattice, stencil, psi, G_self=G_self)
+    sim.step(12)
+    sim.sync()
+    f = sim.populations().cpu().numpy()
+    ref = oracle.step(op, oracle.init(op, nA0, nB0), 12)
+    assert rel(f, ref) < 1e-13
+    nA, nB, u = sim.moments()
+    oA, oB, ou = oracle.moments(op, ref)
+    assert rel(nA.cpu(), oA) < 1e-13 and rel(nB.cpu(), oB) < 1e-13
+    assert np.abs(u.cpu().numpy() - ou).max() < 1e-13 * max(1.0, np.abs(ou).max())
+
+
+@pytest.mark.parametrize("shape,lattice,stencil,psi,G_self", CASES)
+def test_fp32_step_matches_oracle(B, shape, lattice, stencil, psi, G_self):
+    sim, op, nA0, nB0 = setup(B, shape, B.SC_STORE_F32, lattice, stencil, psi, G_self=G_self)
+    sim.step(12)
+    sim.sync()
+    ref = oracle.step(op, oracle.init(op, nA0, nB0), 12)
+    nA, nB, u = sim.moments()
+    oA, oB, ou = oracle.moments(op, ref)
+    assert rel(nA.cpu(), oA) < 1e-6 and rel(nB.cpu(), oB) < 1e-6
+    assert np.abs(u.cpu().numpy() - ou).max() < 1e-6 * (np.abs(ou).max() + 1e-12)
+    assert rel(sim.populations().cpu().numpy(), ref) < 1e-6
+
+
+def test_config1_d2q9_2000_steps(B):
+    """The 64x64 D2Q9 droplet workload (G c_s^2 = 1.4, psi = n, tau = 1), 2000
+    steps, FP64 and FP32 storage against the FP64 oracle."""
+    shape = (64, 64, 1)
+    nA0, nB0 = S.droplet((1, 64, 64), (32, 32, 0), 12.0)
+    kw = dict(tau=(1.0, 1.0), G=4.2, G_self=(0.0, 0.0))
+    op = oracle.Params(shape=shape, lattice=0, psi_self=0, **kw)
+    ref = oracle.step(op, oracle.init(op, nA0, nB0), 2000)
+    oA, oB, ou = oracle.moments(op, ref)
+    for storage, tol in ((B.SC_STORE_F64, 1e-12), (B.SC_STORE_F32, 1e-6)):
+        p = B.make_params(shape, lattice=0, psi_self=0, storage=storage, **kw)
+        sim = B.Simulation(p, nA0, nB0)
+        sim.step(2000)
+        sim.sync()
+        nA, nB, u = sim.moments()
+        assert rel(nA.cpu(), oA) < tol, storage
+        assert rel(nB.cpu(), oB) < tol, storage
+        assert np.abs(u.cpu().numpy() - ou).max() < tol * np.abs(ou).max()
+
+
+@pytest.mark.parametrize("storage", ["F64", "F32"])
+def test_tiling_does_not_change_results(B, storage):
+    """Block shape (tile rows, planes per block) only reorders work: results are bitwise equal."""
+    st = getattr(B, f"SC_STORE_{storage}")
+    outs = []
+    for ty, tz in ((4, 16), (1, 1), (2, 5), (8, 3)):
+        sim, *_ = setup(B, (45, 19, 23), st, tile_y=ty, tile_z=tz)
+        sim.step(7)
+        sim.sync()
+        outs.append(sim.state().cpu().numpy())
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o, outs[0])
+
+
+def test_swap_symmetry_bitwise(B):
+    """Section 2: G_AA = G_BB and tau_A = tau_B make A <-> B an exact symmetry."""
+    shape = (40, 12, 9)
+    nA0, nB0 = S.droplet(shape[::-1], (20, 6, 4), 3.0, n_in=0.85, n_out=0.15)
+    kw = dict(lattice=1, psi_self=1, storage=B.SC_STORE_F32, tau=(0.9, 0.9), G=2.5, G_self=(-0.3, -0.3))
+    a = B.Simulation(B.make_params(shape, **kw), nA0, nB0)
+    b = B.Simulation(B.make_params(shape, **kw), nB0, nA0)
+    a.step(25)
+    b.step(25)
+    fa, fb = a.populations().cpu().numpy(), b.populations().cpu().numpy()
+    np.testing.assert_array_equal(fa[0], fb[1])
+    np.testing.assert_array_equal(fa[1], fb[0])
+
+
+def test_uniform_mixture_stays_uniform(B):
+    shape = (40, 7, 6)
+    for storage in (B.SC_STORE_F32, B.SC_STORE_F16, B.SC_STORE_BF16):
+        p = B.make_params(shape, psi_self=1, storage=storage, tau=(0.7, 1.3), G=3.0, G_self=(-0.5, 0.2))
+        sim = B.Simulation(p, *S.uniform(shape[::-1], 0.37, 0.71))
+        sim.step(30)
+        f = sim.populations().cpu().numpy()
+        assert not np.ptp(f, axis=2).any()
+        nA, nB, u = sim.moments()
+        assert not u.cpu().numpy().any()
+
+
+def test_conservation(B):
+    """Section 2: per-component mass exactly conserved (FP32 storage: drift at
+    round-off level); total momentum conserved for tau_A = tau_B."""
+    sim, op, nA0, nB0 = setup(B, (48, 20, 16), B.SC_STORE_F32, tau=(0.9, 0.9), amp=1e-2)
+    t0 = sim.totals().cpu().numpy()
+    sim.step(200)
+    t1 = sim.totals().cpu().numpy()
+    assert abs(t0[0] - nA0.sum()) < 1e-7 * nA0.sum()
+    assert np.abs(t1[:2] - t0[:2]).max() < 1e-6 * t0[:2].max()
+    assert np.abs(t1[2:]).max() < 1e-6 * t0[:2].sum()
+
+
+def test_checkpoint_resume_bitwise(B):
+    sim, *_ = setup(B, (40, 12, 10), B.SC_STORE_F32)
+    sim.step(5)
+    snap = sim.state().clone()
+    sim.step(9)
+    a = sim.state().cpu().numpy()
+    sim.set_state(snap)
+    sim.step(9)
+    np.testing.assert_array_equal(sim.state().cpu().numpy(), a)
+
+
+def test_set_get_populations_roundtrip(B):
+    sim, op, nA0, nB0 = setup(B, (35, 9, 7), B.SC_STORE_F64)
+    f = oracle.step(op, oracle.init(op, nA0, nB0), 3)
+    sim.set_populations(f)
+    g = sim.populations().cpu().numpy()
+    assert rel(g, f) < 1e-15
+    sim.step(2)
+    assert rel(sim.populations().cpu().numpy(), oracle.step(op, f, 2)) < 1e-13
+
+
+def test_nonpositive_density_is_reported(B):
+    """A state with a negative density makes the step set the status word;
+    sc_sync returns SC_ENAN (a host-side error code, no device fault)."""
+    sim, op, nA0, nB0 = setup(B, (34, 6, 5), B.SC_STORE_F32)
+    f = oracle.init(op, nA0, nB0)
+    f[0, :, 7] = -0.1
+    sim.set_populations(f)
+    sim.step(1)
+    with pytest.raises(B.ScError) as e:
+        sim.sync()
+    assert e.value.status == B.SC_ENAN
+    sim.sync()  # flag cleared
+
+
+# ------------------------------------------------------------ analysis path
+@pytest.mark.parametrize("lattice,stencil", [(1, 0), (1, 1), (0, 0)])
+def test_profiles_match_oracle(B, lattice, stencil):
+    shape = (40, 36, 34) if lattice == 1 else (64, 60, 1)
+    sim, op, nA0, nB0 = setup(B, shape, B.SC_STORE_F64, lattice, stencil, 1, G_self=(-0.4, 0.1), amp=1e-2)
+    sim.step(6)
+    f = sim.populations().cpu().numpy()
+    oA, oB, _ = oracle.moments(op, f, with_u=False)
+    centre = (20.0, 18.0, 17.0) if lattice == 1 else (32.0, 30.0, 0.0)
+    for kind, nbins, bw in ((B.SC_PROFILE_RADIAL, 40, 0.5), (B.SC_PROFILE_PLANAR_Z, shape[2], 1.0),
+                            (B.SC_PROFILE_AXIS_X, 20, 1.0)):
+        got = sim.profile(kind, centre, bw, nbins).cpu().numpy()
+        want = oracle.profile(op, oA, oB, kind, centre, bw, nbins)
+        np.testing.assert_array_equal(got[:, 5], want[:, 5])
+        np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-14)
+    for node in ((0, 0, 0), (shape[0] - 1, shape[1] - 1, shape[2] - 1), (3, 5, 0)):
+        s = node[0] + shape[0] * (node[1] + shape[1] * node[2])
+        assert sim.bulk_pressure(node).item() == pytest.approx(oracle.bulk_pressure(op, oA[s], oB[s]), rel=1e-13)
+
+
+def test_sigma_minimum_matches_oracle(B):
+    import torch
+
+    import oracle.sigma as SG
+
+    r = np.linspace(0.0, 20.0, 81)
+    pt = 0.33 - 0.01 * np.exp(-0.5 * (r - 8.0) ** 2) + 0.004 * (r < 8.0)
+    rows = np.zeros((90, 6))
+    rows[:81, 0] = r
+    rows[:81, 2] = pt
+    rows[:81, 5] = 1.0
+    rows[40, 5] = 0.0  # an empty bin is skipped
+    keep = rows[:, 5] > 0
+    pio = torch.tensor([0.334, 0.330], dtype=torch.float64, device="cuda")
+    out = torch.empty(8, dtype=torch.float64, device="cuda")
+    for dim in (3, 2):
+        B.sc_sigma_minimum(torch.tensor(rows, device="cuda"), pio, dim, 1.0, 19.0, 0.01, out)
+        o = out.cpu().numpy()
+        want = SG.surface_of_tension(rows[keep, 0], rows[keep, 2], 0.334, 0.330, dim=dim)
+        assert o[0] == pytest.approx(want["dP"], rel=1e-15)
+        assert o[1] == pytest.approx(want["C"], rel=1e-13)
+        assert o[2] == pytest.approx(want["Rs"], rel=1e-13)
+        assert o[3] == pytest.approx(want["sigma_s"], rel=1e-13)
+        Rg, sg = SG.argmin_on_grid(rows[keep, 0], rows[keep, 2], 0.334, 0.330, 1.0, 19.0, 0.01, dim=dim)
+        assert o[4] == pytest.approx(Rg, rel=1e-9)
+        assert o[5] == pytest.approx(sg, rel=1e-9)
+
+
+def test_run_host_matches_device_path(B):
+    import torch
+
+    shape = (40, 12, 10)
+    nA0, nB0 = S.droplet(shape[::-1], (20, 6, 5), 3.0, n_in=0.85, n_out=0.15)
+    p = B.make_params(shape, psi_self=1, storage=B.SC_STORE_F32, tau=(1.0, 0.9), G=2.5, G_self=(-0.4, 0.0))
+    ws = torch.empty(B.sc_workspace_bytes(p), dtype=torch.uint8, device="cuda")
+    hA = torch.from_numpy(nA0.reshape(-1)).pin_memory()
+    hB = torch.from_numpy(nB0.reshape(-1)).pin_memory()
+    oA = torch.empty_like(hA).pin_memory()
+    oB = torch.empty_like(hB).pin_memory()
+    B.sc_run_host(p, hA, hB, 11, oA, oB, ws)
+    sim = B.Simulation(p, nA0, nB0)
+    sim.step(11)
+    nA, nB, _ = sim.moments(with_u=False)
+    np.testing.assert_array_equal(oA.numpy(), nA.cpu().numpy())
+    np.testing.assert_array_equal(oB.numpy(), nB.cpu().numpy())
