@@ -29,7 +29,7 @@ METRIC = "MLUPS and % of HBM roofline (D3Q19 2-comp); FP32 vs FP16-storage at st
 SHAPE = (128, 128, 128)
 RADIUS = 24.0
 G_CROSS = 3.6  # G c_s^2 = 1.2: the largest tested coupling that is stable in three dimensions at tau = 1
-INNER = 2048  # time steps per benchmark step (section 4: delta t = 2^11)
+INNER = 2048  # time steps per benchmark step (section 4: delta t = 2^11); --inner overrides for profiling
 BYTES_PER_SITE = {"f32": 304, "f16": 152, "bf16": 152, "f64": 608}  # 2 comps x 19 pops x (read + write) x bytes
 
 
@@ -189,7 +189,8 @@ def run_gpu(args, rank, world, local_rank):
     storage = args.storage
     st = {"f32": B.SC_STORE_F32, "f16": B.SC_STORE_F16, "bf16": B.SC_STORE_BF16, "f64": B.SC_STORE_F64}[storage]
     params = B.make_params(SHAPE, lattice=B.SC_D3Q19, stencil=B.SC_FORCE_E4, psi_self=B.SC_PSI_EXP, storage=st,
-                           tau=(1.0, 1.0), G=G_CROSS, G_self=(0.0, 0.0), tile_y=args.tile_y, tile_z=args.tile_z)
+                           tau=(1.0, 1.0), G=G_CROSS, G_self=(0.0, 0.0), tile_y=args.tile_y, tile_z=args.tile_z,
+                           variant=args.variant)
     nA0, nB0 = fields()
     stream = torch.cuda.Stream(dev)
     sites = SHAPE[0] * SHAPE[1] * SHAPE[2]
@@ -258,7 +259,7 @@ def run_gpu(args, rank, world, local_rank):
 
     # end to end through the host-buffer entry point: H2D of the initial fields, INNER steps, D2H of the densities
     e2e = None
-    if rank == 0 or True:
+    if not args.no_e2e:
         ws = sim.workspace  # reuse the device workspace (the simulation above is finished)
         hA = torch.from_numpy(nA0.reshape(-1)).pin_memory()
         hB = torch.from_numpy(nB0.reshape(-1)).pin_memory()
@@ -293,6 +294,7 @@ def run_gpu(args, rank, world, local_rank):
 
 
 def main():
+    global INNER
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -301,10 +303,14 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "f64"])
     ap.add_argument("--tile-y", type=int, default=0)
     ap.add_argument("--tile-z", type=int, default=0)
+    ap.add_argument("--variant", type=int, default=0, help="step kernel: 0 auto, 1 generic, 2 TMA-staged")
     ap.add_argument("--kernel-events", action="store_true", help="record per-step kernel events in the timed loop")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--inner", type=int, default=INNER, help="time steps per benchmark step (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
+    INNER = args.inner
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

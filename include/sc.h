@@ -45,7 +45,9 @@ typedef enum {
   SC_EINVAL = 1,        /* bad argument (null pointer, size, parameter out of range) */
   SC_ENOMEM = 2,        /* workspace smaller than sc_workspace_bytes() */
   SC_ECUDA = 3,         /* a CUDA runtime call failed (message has the CUDA error) */
-  SC_ENAN = 4,          /* a kernel met a non-positive or non-finite density */
+  SC_ENAN = 4,          /* a step met a non-finite density, or a non-positive one while
+                           psi = exp(-1/n) is in use (with psi = n the method stays defined
+                           for transiently negative densities, and they are not flagged) */
   SC_ETIMEOUT = 5,      /* a bounded device-side wait ran out */
   SC_EUNSUPPORTED = 6   /* valid request this build does not implement */
 } sc_status;
@@ -60,7 +62,9 @@ typedef enum { SC_PSI_N = 0, SC_PSI_EXP = 1 } sc_psi;
 /* Population storage.  Stored values are deviations g_i = f_i - w_i nbar_J from
  * a rest equilibrium with the mean initial density nbar_J; F16/BF16 store
  * g_i * 2^k(J,i) with a power-of-two scale fixed at sc_create.  Collision
- * arithmetic is FP32 for F32/F16/BF16 and FP64 for F64. */
+ * arithmetic is FP32 for F32/F16/BF16 and FP64 for F64.  In device memory the
+ * two components of a direction and site are adjacent ([i][site][J]); this raw
+ * layout is what sc_get_state / sc_set_state copy. */
 typedef enum { SC_STORE_F32 = 0, SC_STORE_F16 = 1, SC_STORE_BF16 = 2, SC_STORE_F64 = 3 } sc_storage;
 typedef enum { SC_PROFILE_RADIAL = 0, SC_PROFILE_PLANAR_Z = 1, SC_PROFILE_AXIS_X = 2 } sc_profile_kind;
 
@@ -73,8 +77,10 @@ typedef struct {
   int32_t psi_self;    /* sc_psi */
   int32_t storage;     /* sc_storage */
   int32_t tile_y;      /* step-kernel tile rows (1, 2, 4 or 8); 0 = library default */
-  int32_t tile_z;      /* planes per step-kernel block (>= 1); 0 = library default */
-  int32_t reserved;    /* must be 0 */
+  int32_t tile_z;      /* planes per step-kernel work item (>= 1); 0 = library default */
+  int32_t variant;     /* step kernel: 0 = automatic, 1 = generic (any size, any stencil),
+                          2 = cp.async-staged (D3Q19, E4, nx % 32 == 0, nx >= 64,
+                          tile_y 4 or 8; tile_y 4 for F64); both compute the same numbers */
   double tau[2];       /* tau_A, tau_B > 1/2 (Eq. omega_i) */
   double G;            /* inter-component coupling G */
   double G_self[2];    /* self couplings G_AA, G_BB */
@@ -152,8 +158,8 @@ sc_status sc_sigma_minimum(const double *rows, int32_t nbins, const double *P_in
  * momentum x, y, z) summed over the lattice (section 2).  Asynchronous. */
 sc_status sc_totals(sc_ctx *ctx, double *out);
 
-/* Wait for the context's stream and report device-side errors (SC_ENAN when a
- * step met a non-positive or non-finite density; the flag is then cleared). */
+/* Wait for the context's stream and report device-side errors (SC_ENAN, see
+ * sc_status; the flag is then cleared). */
 sc_status sc_sync(sc_ctx *ctx);
 
 /* Convenience entry point with HOST buffers: create, run nsteps and read the

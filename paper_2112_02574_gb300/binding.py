@@ -37,17 +37,17 @@ class sc_params(ctypes.Structure):
         ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
         ("lattice", ctypes.c_int32), ("stencil", ctypes.c_int32), ("psi_self", ctypes.c_int32),
         ("storage", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("tile_z", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("variant", ctypes.c_int32),
         ("tau", ctypes.c_double * 2), ("G", ctypes.c_double), ("G_self", ctypes.c_double * 2),
     ]
 
 
 def make_params(shape, lattice=SC_D3Q19, stencil=SC_FORCE_E4, psi_self=SC_PSI_EXP, storage=SC_STORE_F32,
-                tau=(1.0, 1.0), G=0.0, G_self=(0.0, 0.0), tile_y=0, tile_z=0) -> sc_params:
-    """sc_params for a lattice of shape (nx, ny, nz)."""
+                tau=(1.0, 1.0), G=0.0, G_self=(0.0, 0.0), tile_y=0, tile_z=0, variant=0) -> sc_params:
+    """sc_params for a lattice of shape (nx, ny, nz); variant 0 auto, 1 generic, 2 staged step kernel."""
     nx, ny, nz = shape
     return sc_params(int(nx), int(ny), int(nz), int(lattice), int(stencil), int(psi_self), int(storage),
-                     int(tile_y), int(tile_z), 0, (ctypes.c_double * 2)(*tau), float(G),
+                     int(tile_y), int(tile_z), int(variant), (ctypes.c_double * 2)(*tau), float(G),
                      (ctypes.c_double * 2)(*G_self))
 
 

@@ -51,6 +51,12 @@ size_t store_bytes(int storage) {
   }
 }
 
+bool staged_eligible(const sc_params *p, int tile_y) {
+  if (p->lattice != SC_D3Q19 || p->stencil != SC_FORCE_E4 || p->nx % 32 != 0 || p->nx < 64) return false;
+  if (p->storage == SC_STORE_F64) return tile_y == 4;
+  return tile_y == 4 || tile_y == 8;
+}
+
 sc_status validate(const sc_params *p) {
   if (!p) return fail(SC_EINVAL, "params is NULL");
   if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(SC_EINVAL, "lattice size must be >= 1 in every direction");
@@ -65,7 +71,10 @@ sc_status validate(const sc_params *p) {
   if (p->tile_y != 0 && p->tile_y != 1 && p->tile_y != 2 && p->tile_y != 4 && p->tile_y != 8)
     return fail(SC_EINVAL, "tile_y must be 0, 1, 2, 4 or 8");
   if (p->tile_z < 0) return fail(SC_EINVAL, "tile_z must be >= 0");
-  if (p->reserved != 0) return fail(SC_EINVAL, "reserved must be 0");
+  if (p->variant < 0 || p->variant > 2) return fail(SC_EINVAL, "variant must be 0, 1 or 2");
+  if (p->variant == 2 && !staged_eligible(p, p->tile_y ? p->tile_y : 4))
+    return fail(SC_EINVAL, "the staged step kernel needs D3Q19, E4, nx %% 32 == 0, nx >= 64 and tile_y 4 or 8 "
+                           "(4 for F64 storage)");
   for (int J = 0; J < 2; ++J)
     if (!(p->tau[J] > 0.5) || !isfinite(p->tau[J])) return fail(SC_EINVAL, "tau[%d] must be > 1/2", J);
   if (!isfinite(p->G) || !isfinite(p->G_self[0]) || !isfinite(p->G_self[1]))
@@ -97,11 +106,20 @@ Layout layout_of(const sc_params *p) {
   return L;
 }
 
-int default_tile_y(const sc_params *p) { return p->tile_y ? p->tile_y : 4; }
+// Kernel choice and tiles (a measured sweep at 128^3 set the defaults).
+bool use_staged(const sc_params *p) {
+  if (p->variant == 1) return false;
+  return staged_eligible(p, p->tile_y ? p->tile_y : 4);
+}
+int default_tile_y(const sc_params *p) {
+  if (p->tile_y) return p->tile_y;
+  if (use_staged(p)) return 4;
+  return p->lattice == SC_D3Q19 ? 8 : 4;
+}
 int default_tile_z(const sc_params *p) {
   if (p->lattice == SC_D2Q9) return 1;
-  if (p->tile_z) return p->tile_z < p->nz ? p->tile_z : p->nz;
-  return p->nz < 16 ? p->nz : 16;
+  const int want = p->tile_z ? p->tile_z : (use_staged(p) ? 16 : 32);
+  return want < p->nz ? want : p->nz;
 }
 
 }  // namespace
@@ -115,6 +133,7 @@ struct sc_ctx {
   Layout L;
   int cur;  // buffer holding the current state
   int tile_y, tile_z;
+  int staged;
   double nbar[2], psibar[2];
   double scale[2][19], inv_scale[2][19];
   int64_t launches;
@@ -193,6 +212,14 @@ sc_status ensure_fields(sc_ctx *c) {
 }
 
 template <class CT>
+P2<CT> pair(double a, double b) {
+  P2<CT> p;
+  p.x = CT(a);
+  p.y = CT(b);
+  return p;
+}
+
+template <class CT>
 StepArgs<CT> step_args(sc_ctx *c) {
   StepArgs<CT> a;
   memset(&a, 0, sizeof(a));
@@ -204,16 +231,14 @@ StepArgs<CT> step_args(sc_ctx *c) {
   a.tile_z = c->tile_z;
   a.N = c->N;
   const double cs2 = 1.0 / 3.0;
-  for (int J = 0; J < 2; ++J) {
-    a.nbar[J] = CT(c->nbar[J]);
-    a.omega[J] = CT(1.0 / c->p.tau[J]);
-    a.guo[J] = CT(1.0 - 0.5 / c->p.tau[J]);
-    a.gself[J] = CT(-c->p.G_self[J] * cs2);
-    a.psibar[J] = CT(c->psibar[J]);
-    for (int i = 0; i < 19; ++i) {
-      a.scale[J][i] = CT(c->scale[J][i]);
-      a.inv_scale[J][i] = CT(c->inv_scale[J][i]);
-    }
+  a.nbar = pair<CT>(c->nbar[0], c->nbar[1]);
+  a.omega = pair<CT>(1.0 / c->p.tau[0], 1.0 / c->p.tau[1]);
+  a.guo = pair<CT>(1.0 - 0.5 / c->p.tau[0], 1.0 - 0.5 / c->p.tau[1]);
+  a.gself = pair<CT>(-c->p.G_self[0] * cs2, -c->p.G_self[1] * cs2);
+  a.psibar = pair<CT>(c->psibar[0], c->psibar[1]);
+  for (int i = 0; i < 19; ++i) {
+    a.scale[i] = pair<CT>(c->scale[0][i], c->scale[1][i]);
+    a.inv_scale[i] = pair<CT>(c->inv_scale[0][i], c->inv_scale[1][i]);
   }
   a.gcross = CT(-c->p.G * cs2);
   a.self_on = (c->p.G_self[0] != 0.0 || c->p.G_self[1] != 0.0) ? 1 : 0;
@@ -227,6 +252,7 @@ sc_status launch_one_step(sc_ctx *c) {
   l.lattice = c->p.lattice == SC_D3Q19 ? kD3Q19 : kD2Q9;
   l.stencil = c->p.stencil == SC_FORCE_E6 ? kE6 : kE4;
   l.tile_y = c->tile_y;
+  l.staged = c->staged;
   l.grid = dim3((c->p.nx + 31) / 32, (c->p.ny + c->tile_y - 1) / c->tile_y, (c->p.nz + c->tile_z - 1) / c->tile_z);
   l.stream = c->stream;
   cudaError_t e;
@@ -324,6 +350,7 @@ sc_status sc_create(const sc_params *params, const double *nA0, const double *nB
   c->cur = 0;
   c->tile_y = default_tile_y(params);
   c->tile_z = default_tile_z(params);
+  c->staged = use_staged(params) ? 1 : 0;
   c->fields_at = -1;
   double mean[2], maxdev[2];
   cudaError_t e = cudaMemsetAsync(c->ws + L.off_status, 0, kStatusBytes, c->stream);
@@ -523,7 +550,8 @@ sc_status sc_sync(sc_ctx *c) {
   SC_CUDA(cudaMemcpy(&w, status_word(c), sizeof(w), cudaMemcpyDeviceToHost));
   if (w) {
     SC_CUDA(cudaMemset(status_word(c), 0, sizeof(unsigned int)));
-    return fail(SC_ENAN, "a time step met a non-positive or non-finite density (status 0x%x)", w);
+    return fail(SC_ENAN, "a time step met a non-finite density, or a non-positive one with psi = exp(-1/n) "
+                         "(status 0x%x)", w);
   }
   return SC_OK;
 }

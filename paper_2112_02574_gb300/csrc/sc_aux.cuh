@@ -9,21 +9,30 @@
 namespace scgb {
 
 // Storage read / write in FP64 (natural populations f = g / scale + w nbar).
+// Populations are component-interleaved: element (i * N + s) * 2 + J.
+__device__ __forceinline__ double to_double(float v) { return v; }
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ double to_double(__half v) { return __half2float(v); }
+__device__ __forceinline__ double to_double(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <class ST>
+__device__ __forceinline__ ST from_double(double v);
+template <>
+__device__ __forceinline__ float from_double<float>(double v) { return float(v); }
+template <>
+__device__ __forceinline__ double from_double<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ __half from_double<__half>(double v) { return __float2half_rn(float(v)); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_double<__nv_bfloat16>(double v) {
+  return __float2bfloat16_rn(float(v));
+}
 template <class ST>
 __device__ __forceinline__ double load_dev(const ST *p, double inv_scale) {
-  return double(Codec<ST, float>::load(p, 1.0f)) * inv_scale;
-}
-template <>
-__device__ __forceinline__ double load_dev<double>(const double *p, double inv_scale) {
-  return __ldg(p) * inv_scale;
+  return to_double(*p) * inv_scale;
 }
 template <class ST>
 __device__ __forceinline__ void store_dev(ST *p, double v, double scale) {
-  Codec<ST, float>::store(p, float(v * scale), 1.0f);
-}
-template <>
-__device__ __forceinline__ void store_dev<double>(double *p, double v, double scale) {
-  *p = v * scale;
+  *p = from_double<ST>(v * scale);
 }
 
 struct PopArgs {
@@ -69,15 +78,15 @@ __global__ void pop_kernel(PopArgs a, int mode, const double *n0A, const double 
         const double w = L::w(i);
         const int64_t fwd = site_at(x + cx, y + cy, z + cz, a.nx, a.ny, a.nz);
         const int64_t bwd = site_at(x - cx, y - cy, z - cz, a.nx, a.ny, a.nz);
-        ST *slot = buf + ((int64_t)J * L::Q + i) * N;
+        ST *slot = buf + (int64_t)i * N * 2 + J;
         if (mode == 0) {
           const double n = (J == 0 ? n0A : n0B)[fwd];
-          store_dev<ST>(slot + s, w * (n - a.nbar[J]), a.scale[J][i]);
+          store_dev<ST>(slot + s * 2, w * (n - a.nbar[J]), a.scale[J][i]);
         } else if (mode == 1) {
           const double fv = f[((int64_t)J * L::Q + i) * N + fwd];
-          store_dev<ST>(slot + s, fv - w * a.nbar[J], a.scale[J][i]);
+          store_dev<ST>(slot + s * 2, fv - w * a.nbar[J], a.scale[J][i]);
         } else {
-          f[((int64_t)J * L::Q + i) * N + s] = load_dev<ST>(slot + bwd, a.inv_scale[J][i]) + w * a.nbar[J];
+          f[((int64_t)J * L::Q + i) * N + s] = load_dev<ST>(slot + bwd * 2, a.inv_scale[J][i]) + w * a.nbar[J];
         }
       }
     }
@@ -100,7 +109,7 @@ __global__ void fields_kernel(PopArgs a, int psi_exp, double *fields) {
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) {
         const int64_t bwd = site_at(x - L::c(i, 0), y - L::c(i, 1), z - L::c(i, 2), a.nx, a.ny, a.nz);
-        dn += load_dev<ST>(buf + ((int64_t)J * L::Q + i) * N + bwd, a.inv_scale[J][i]);
+        dn += load_dev<ST>(buf + ((int64_t)i * N + bwd) * 2 + J, a.inv_scale[J][i]);
       }
       const double n = a.nbar[J] + dn;
       fields[J * N + s] = n;
@@ -165,7 +174,7 @@ __global__ void velocity_kernel(PopArgs a, ForceParams fp, const double *fields,
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) {
         const int64_t bwd = site_at(x - L::c(i, 0), y - L::c(i, 1), z - L::c(i, 2), a.nx, a.ny, a.nz);
-        const double g = load_dev<ST>(buf + ((int64_t)J * L::Q + i) * N + bwd, a.inv_scale[J][i]);
+        const double g = load_dev<ST>(buf + ((int64_t)i * N + bwd) * 2 + J, a.inv_scale[J][i]);
 #pragma unroll
         for (int m = 0; m < 3; ++m) j[J][m] += L::c(i, m) * g;
       }
@@ -227,7 +236,7 @@ struct ProfileArgs {
 template <int LAT, int STEN>
 __global__ void __launch_bounds__(32) profile_partial_kernel(ForceParams fp, ProfileArgs pa, const double *fields,
                                                              double *partial) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   double *bins = reinterpret_cast<double *>(smem_raw);
   const int lane = threadIdx.x;
   for (int k = lane; k < pa.nbins * 6; k += 32) bins[k] = 0.0;
@@ -416,7 +425,7 @@ __global__ void __launch_bounds__(256) totals_partial_kernel(PopArgs a, double *
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) {
         // stored at the collision site: sums over all sites need no pull
-        const double f = load_dev<ST>(buf + ((int64_t)J * L::Q + i) * N + s, a.inv_scale[J][i]) + L::w(i) * a.nbar[J];
+        const double f = load_dev<ST>(buf + ((int64_t)i * N + s) * 2 + J, a.inv_scale[J][i]) + L::w(i) * a.nbar[J];
         acc[J] += f;
 #pragma unroll
         for (int m = 0; m < 3; ++m) acc[2 + m] += L::c(i, m) * f;

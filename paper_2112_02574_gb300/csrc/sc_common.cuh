@@ -1,8 +1,14 @@
 // Device-side building blocks shared by the kernels of this library:
-// velocity sets, forcing stencils, storage codecs and kernel argument structs.
+// velocity sets, forcing stencils, component-pair arithmetic, storage codecs
+// and kernel argument structs.
 //
 // Model: two-component Shan-Chen lattice Boltzmann method of arXiv:2112.02574,
 // section 2 (Eqs. lbm, omega_i, Guo, feq, u, sc_force), c_s^2 = 1/3.
+//
+// Population storage is component-interleaved: the value of component J in
+// direction i at site s sits at element (i * N + s) * 2 + J, so one access
+// carries both components of a direction and site (8 bytes in FP32), and the
+// two components are computed together with paired (FP32x2) arithmetic.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -15,6 +21,55 @@
 namespace scgb {
 
 constexpr int kD2Q9 = 0, kD3Q19 = 1;
+
+// ------------------------------------------------------------ arithmetic
+// Explicitly rounded arithmetic: the step kernels spell every operation of the
+// collision with these, so kernels of different shape produce bitwise identical
+// results whatever the compiler would otherwise contract.
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float rdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double rdiv(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float expm1_ct(float x) { return expm1f(x); }
+__device__ __forceinline__ double expm1_ct(double x) { return expm1(x); }
+
+// Component pairs (x = A, y = B).  FP32 pairs use the packed FP32x2 operations
+// of sm_100+ (each lane rounded exactly like its scalar counterpart).
+template <class CT>
+struct Pair;
+template <>
+struct Pair<float> {
+  using T = float2;
+};
+template <>
+struct Pair<double> {
+  using T = double2;
+};
+template <class CT>
+using P2 = typename Pair<CT>::T;
+
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 pset(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 pbc(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 pswap(float2 a) { return make_float2(a.y, a.x); }
+__device__ __forceinline__ double2 padd(double2 a, double2 b) { return make_double2(radd(a.x, b.x), radd(a.y, b.y)); }
+__device__ __forceinline__ double2 psub(double2 a, double2 b) { return make_double2(rsub(a.x, b.x), rsub(a.y, b.y)); }
+__device__ __forceinline__ double2 pmul(double2 a, double2 b) { return make_double2(rmul(a.x, b.x), rmul(a.y, b.y)); }
+__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c) {
+  return make_double2(rfma(a.x, b.x, c.x), rfma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ double2 pset(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ double2 pbc(double s) { return make_double2(s, s); }
+__device__ __forceinline__ double2 pswap(double2 a) { return make_double2(a.y, a.x); }
 
 // ---------------------------------------------------------------- lattices
 // D3Q19 velocities, opposite directions adjacent (the order sc.h documents).
@@ -102,27 +157,51 @@ struct Stencil<kD3Q19, kE6> {
 };
 
 // ---------------------------------------------------------------- storage
-// Stored value -> compute type and back.  F16/BF16 carry a per-(J, i)
-// power-of-two scale so that the deviations sit in the normal range.
-template <class S, class CT>
-struct Codec {
-  __device__ __forceinline__ static CT load(const S *p, CT /*inv_scale*/) { return CT(__ldg(p)); }
-  __device__ __forceinline__ static void store(S *p, CT v, CT /*scale*/) { *p = S(v); }
+// A component pair (A, B) of one direction and site: stored -> compute pair and
+// back.  F16/BF16 carry a per-(J, i) power-of-two scale so that the deviations
+// sit in the normal range.  SMEM selects plain loads (shared memory) instead of
+// read-only-cache loads (global memory).
+template <class ST, class CT>
+struct Codec2;
+template <>
+struct Codec2<float, float> {
+  template <bool SMEM>
+  __device__ __forceinline__ static float2 load(const float *p, float2) {
+    return SMEM ? *reinterpret_cast<const float2 *>(p) : __ldg(reinterpret_cast<const float2 *>(p));
+  }
+  __device__ __forceinline__ static void store(float *p, float2 v, float2) { *reinterpret_cast<float2 *>(p) = v; }
 };
 template <>
-struct Codec<__half, float> {
-  __device__ __forceinline__ static float load(const __half *p, float inv_scale) {
-    return __half2float(__ldg(p)) * inv_scale;
+struct Codec2<double, double> {
+  template <bool SMEM>
+  __device__ __forceinline__ static double2 load(const double *p, double2) {
+    return SMEM ? *reinterpret_cast<const double2 *>(p) : __ldg(reinterpret_cast<const double2 *>(p));
   }
-  __device__ __forceinline__ static void store(__half *p, float v, float scale) { *p = __float2half_rn(v * scale); }
+  __device__ __forceinline__ static void store(double *p, double2 v, double2) {
+    *reinterpret_cast<double2 *>(p) = v;
+  }
 };
 template <>
-struct Codec<__nv_bfloat16, float> {
-  __device__ __forceinline__ static float load(const __nv_bfloat16 *p, float inv_scale) {
-    return __bfloat162float(__ldg(p)) * inv_scale;
+struct Codec2<__half, float> {
+  template <bool SMEM>
+  __device__ __forceinline__ static float2 load(const __half *p, float2 inv_scale) {
+    const __half2 h = SMEM ? *reinterpret_cast<const __half2 *>(p) : __ldg(reinterpret_cast<const __half2 *>(p));
+    return pmul(__half22float2(h), inv_scale);
   }
-  __device__ __forceinline__ static void store(__nv_bfloat16 *p, float v, float scale) {
-    *p = __float2bfloat16_rn(v * scale);
+  __device__ __forceinline__ static void store(__half *p, float2 v, float2 scale) {
+    *reinterpret_cast<__half2 *>(p) = __float22half2_rn(pmul(v, scale));
+  }
+};
+template <>
+struct Codec2<__nv_bfloat16, float> {
+  template <bool SMEM>
+  __device__ __forceinline__ static float2 load(const __nv_bfloat16 *p, float2 inv_scale) {
+    const __nv_bfloat162 h =
+        SMEM ? *reinterpret_cast<const __nv_bfloat162 *>(p) : __ldg(reinterpret_cast<const __nv_bfloat162 *>(p));
+    return pmul(__bfloat1622float2(h), inv_scale);
+  }
+  __device__ __forceinline__ static void store(__nv_bfloat16 *p, float2 v, float2 scale) {
+    *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(pmul(v, scale));
   }
 };
 
@@ -132,22 +211,19 @@ struct StepArgs {
   const void *src;  // populations (post-collision of the previous step, stored at the collision site)
   void *dst;
   int nx, ny, nz, tile_z;
-  int64_t N;        // sites = plane stride
-  CT nbar[2];       // storage reference densities
-  CT omega[2];      // 1 / tau_J
-  CT guo[2];        // 1 - 1 / (2 tau_J)
-  CT gcross;        // -G c_s^2
-  CT gself[2];      // -G_JJ c_s^2
-  CT psibar[2];     // psi(nbar_J)
-  int self_on;      // any G_JJ != 0
-  int psi_exp;      // psi = exp(-1/n) (else psi = n)
-  CT scale[2][19];      // storage scale 2^k (1 for F32/F64)
-  CT inv_scale[2][19];  // 2^-k
-  unsigned int *err;    // device status word (bit 0: non-positive density)
+  int64_t N;         // sites
+  P2<CT> nbar;       // storage reference densities (A, B)
+  P2<CT> omega;      // 1 / tau_J
+  P2<CT> guo;        // 1 - 1 / (2 tau_J)
+  CT gcross;         // -G c_s^2
+  P2<CT> gself;      // -G_JJ c_s^2
+  P2<CT> psibar;     // psi(nbar_J)
+  int self_on;       // any G_JJ != 0
+  int psi_exp;       // psi = exp(-1/n) (else psi = n)
+  P2<CT> scale[19];      // storage scale 2^k(J, i) (1 for F32/F64)
+  P2<CT> inv_scale[19];  // 2^-k(J, i)
+  unsigned int *err;     // device status word (bit 0: density out of range)
 };
-
-__device__ __forceinline__ float expm1_ct(float x) { return expm1f(x); }
-__device__ __forceinline__ double expm1_ct(double x) { return expm1(x); }
 
 __host__ __device__ __forceinline__ int wrapi(int a, int n) {
   // a in [-n, 2n)

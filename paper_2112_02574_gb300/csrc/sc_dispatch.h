@@ -11,7 +11,8 @@ struct StepLaunch {
   int lattice;  // kD2Q9 / kD3Q19
   int stencil;  // kE4 / kE6
   int tile_y;   // 1, 2, 4 or 8
-  dim3 grid;
+  int staged;   // 1: TMA-staged persistent kernel (D3Q19, E4, nx % 32 == 0, nx >= 64)
+  dim3 grid;    // generic kernel grid
   cudaStream_t stream;
 };
 

@@ -4,6 +4,7 @@
 
 #include "sc_dispatch.h"
 #include "sc_step_kernel.cuh"
+#include "sc_step_staged.cuh"
 
 namespace scgb {
 
@@ -21,6 +22,32 @@ cudaError_t launch_one(const StepLaunch &l, const StepArgs<CT> &a) {
   return cudaGetLastError();
 }
 
+// Staged kernel: one block per (x column, y column, z chunk), like the generic kernel.
+template <class ST, class CT, int TY>
+cudaError_t launch_staged_one(const StepLaunch &l, const StepArgs<CT> &a) {
+  constexpr size_t smem = staged_smem_bytes<ST, CT, TY>();
+  auto *k = sc_step_staged<ST, CT, TY>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const dim3 grid(a.nx / 32, (a.ny + TY - 1) / TY, (a.nz + a.tile_z - 1) / a.tile_z);
+  k<<<grid, dim3(32, TY), smem, l.stream>>>(a);
+  return cudaGetLastError();
+}
+
+template <class ST, class CT>
+cudaError_t launch_staged(const StepLaunch &l, const StepArgs<CT> &a) {
+  if (l.lattice != kD3Q19 || l.stencil != kE4 || a.nx % 32 != 0 || a.nx < 64) return cudaErrorInvalidValue;
+  if (l.tile_y == 4) return launch_staged_one<ST, CT, 4>(l, a);
+  if constexpr (sizeof(ST) < 8) {
+    if (l.tile_y == 8) return launch_staged_one<ST, CT, 8>(l, a);
+  }
+  return cudaErrorInvalidValue;
+}
+
 template <int LAT, int STEN, class ST, class CT>
 cudaError_t launch_ty(const StepLaunch &l, const StepArgs<CT> &a) {
   switch (l.tile_y) {
@@ -34,6 +61,7 @@ cudaError_t launch_ty(const StepLaunch &l, const StepArgs<CT> &a) {
 
 template <class ST, class CT>
 cudaError_t launch_any(const StepLaunch &l, const StepArgs<CT> &a) {
+  if (l.staged) return launch_staged<ST, CT>(l, a);
   if (l.lattice == kD3Q19 && l.stencil == kE4) return launch_ty<kD3Q19, kE4, ST, CT>(l, a);
   if (l.lattice == kD3Q19 && l.stencil == kE6) return launch_ty<kD3Q19, kE6, ST, CT>(l, a);
   if (l.lattice == kD2Q9 && l.stencil == kE4) return launch_ty<kD2Q9, kE4, ST, CT>(l, a);

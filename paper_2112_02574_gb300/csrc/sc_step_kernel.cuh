@@ -8,7 +8,9 @@
 //   velocity        n u = sum_J (j_J + F_J / 2)                      (Eq. u)
 //   BGK + Guo       f* = f - (f - f^eq)/tau_J + (1 - 1/(2 tau_J)) F_i (Eqs. omega_i, Guo, feq)
 // The state kept in memory is f* at the collision site, so the next step
-// pulls again; populations are stored as deviations g = f - w_i nbar_J.
+// pulls again; populations are stored as deviations g = f - w_i nbar_J, both
+// components of a direction and site side by side, and every quantity that
+// exists per component is computed as an (A, B) pair.
 //
 // Blocking (the force at x needs n at x + xi_a for the same time level, and
 // those come from other sites' streamed populations): a block owns a column
@@ -25,133 +27,193 @@
 
 namespace scgb {
 
-// Pull the Q populations of component J arriving at site (gx, gy, gz) and
-// return their sum (the density deviation); values go to v[] when V is true.
+// Pull the Q population pairs arriving at site (gx, gy, gz) and return their
+// sum (the density deviations); values go to v[] when V is true.
 template <int LAT, class ST, class CT, bool V>
-__device__ __forceinline__ CT pull_site(const ST *__restrict__ src, int J, int gx, int gy, int gz, int nx, int ny,
-                                        int nz, int64_t N, const CT *inv_scale, CT *v) {
+__device__ __forceinline__ P2<CT> pull_site(const ST *__restrict__ src, int gx, int gy, int gz, int nx, int ny,
+                                            int nz, int64_t N, const P2<CT> *inv_scale, P2<CT> *v) {
   using L = Lattice<LAT>;
   // source coordinate for velocity component c is g - c
   const int X[3] = {wrapi(gx + 1, nx), gx, wrapi(gx - 1, nx)};
   const int Y[3] = {wrapi(gy + 1, ny), gy, wrapi(gy - 1, ny)};
   const int Z[3] = {wrapi(gz + 1, nz), gz, wrapi(gz - 1, nz)};
-  const ST *base = src + (int64_t)J * L::Q * N;
-  CT sum = CT(0);
+  P2<CT> sum = pbc(CT(0));
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
     const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
     const int site = X[cx + 1] + nx * (Y[cy + 1] + ny * Z[cz + 1]);
-    const CT g = Codec<ST, CT>::load(base + (int64_t)i * N + site, inv_scale[i]);
+    const P2<CT> g = Codec2<ST, CT>::template load<false>(src + ((int64_t)i * N + site) * 2, inv_scale[i]);
     if (V) v[i] = g;
-    sum += g;
+    sum = padd(sum, g);
   }
   return sum;
 }
 
+// psi(n) - psi(nbar) per component; for psi = exp(-1/n): psibar * expm1((n - nbar) / (n nbar)).
 template <class CT>
-__device__ __forceinline__ CT psi_deviation(CT dn, CT nbar, CT psibar, int psi_exp) {
-  // psi(n) - psi(nbar); for psi = exp(-1/n): psibar * expm1((n - nbar) / (n nbar))
+__device__ __forceinline__ P2<CT> psi_deviation(P2<CT> dn, P2<CT> nbar, P2<CT> psibar, int psi_exp) {
   if (!psi_exp) return dn;
-  const CT n = nbar + dn;
-  return psibar * expm1_ct(dn / (n * nbar));
+  const P2<CT> n = padd(nbar, dn);
+  const P2<CT> q = pmul(n, nbar);
+  return pmul(psibar, pset(expm1_ct(rdiv(dn.x, q.x)), expm1_ct(rdiv(dn.y, q.y))));
 }
 
-// Shared-memory bytes of one block: density and psi deviations, both
-// components, a ring of planes of (32 + 2 HALO) x (TY + 2 HALO) sites.
+// Shared-memory bytes of one block: density and psi deviation pairs, a ring of
+// planes of (32 + 2 HALO) x (TY + 2 HALO) sites.
 template <int LAT, int STEN, class CT, int TY>
 constexpr size_t step_smem_bytes() {
   constexpr int H = Stencil<LAT, STEN>::HALO;
   constexpr int HZ = (LAT == kD3Q19) ? H : 0;
   constexpr int NPL = (HZ == 0) ? 1 : 2 * HZ + 2;
-  return sizeof(CT) * 2 * 2 * NPL * (32 + 2 * H) * (TY + 2 * H);
+  return sizeof(P2<CT>) * 2 * NPL * (32 + 2 * H) * (TY + 2 * H);
 }
 
-// Collision of one site from its arriving populations g[J][i] and the ring of
-// density / psi deviation planes (Eqs. sc_force, u, feq, Guo, omega_i, lbm).
-template <int LAT, int STEN, class ST, class CT, int TY>
-__device__ __forceinline__ void collide_site(const StepArgs<CT> &a, const CT (&g)[2][Lattice<LAT>::Q],
-                                             const CT *s_dn, const CT *s_psi, const int *sl, int own,
-                                             bool valid, ST *__restrict__ dst, int64_t site) {
-  using L = Lattice<LAT>;
+// ---- the collision (Eqs. sc_force, u, feq, Guo, omega_i, lbm) on component pairs
+// Ring layout: s_dn / s_psi [NPL][PLANE] pairs, PLANE = (32 + 2 HALO) x (TY + 2 HALO);
+// sl[d] is the ring slot of plane c - HZ + d.
+
+// Forces (Eq. sc_force):
+//   F_A = -G c_s^2 n_A sum_a W xi_a n_B(x + xi_a) - G_AA c_s^2 psi_A sum_a W xi_a psi_A(x + xi_a)
+//   F_B = (A <-> B),
+// each +/- stencil pair taken as one difference of deviations.
+template <int LAT, int STEN, class CT, int TY>
+__device__ __forceinline__ void force_pair(const StepArgs<CT> &a, const P2<CT> *s_dn, const P2<CT> *s_psi,
+                                           const int *sl, int own, P2<CT> n, P2<CT> psi, P2<CT> (&F)[3]) {
   using SN = Stencil<LAT, STEN>;
-  constexpr int Q = L::Q;
   constexpr int H = SN::HALO;
   constexpr int HZ = (LAT == kD3Q19) ? H : 0;
-  constexpr int NPL = (HZ == 0) ? 1 : 2 * HZ + 2;
   constexpr int SX = 32 + 2 * H;
   constexpr int PLANE = SX * (TY + 2 * H);
-  const int64_t N = a.N;
-  auto DN = [&](int J, int z, int i) { return s_dn[(J * NPL + z) * PLANE + i]; };
-  auto PS = [&](int J, int z, int i) { return s_psi[(J * NPL + z) * PLANE + i]; };
-
-  CT dn[2], n[2], psi[2];
-#pragma unroll
-  for (int J = 0; J < 2; ++J) {
-    dn[J] = DN(J, sl[HZ], own);
-    n[J] = a.nbar[J] + dn[J];
-    psi[J] = a.self_on ? a.psibar[J] + PS(J, sl[HZ], own) : CT(0);
-  }
-  // Eq. sc_force: S_J = sum_a W xi_a n_J(x + xi_a), T_J = sum_a W xi_a psi_J(x + xi_a),
-  // each +/- pair taken as one difference
-  CT S[2][3] = {{0, 0, 0}, {0, 0, 0}}, T[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  P2<CT> S[3] = {pbc(CT(0)), pbc(CT(0)), pbc(CT(0))}, T[3] = {pbc(CT(0)), pbc(CT(0)), pbc(CT(0))};
 #pragma unroll
   for (int k = 0; k < SN::NH; ++k) {
     const int vx = SN::v(k, 0), vy = SN::v(k, 1), vz = SN::v(k, 2);
-    const CT W = CT(SN::W(k));
     const int ip = own + vy * SX + vx, im = own - vy * SX - vx;
-    const int zp = sl[HZ + vz], zm = sl[HZ - vz];
-#pragma unroll
-    for (int J = 0; J < 2; ++J) {
-      const CT d = DN(J, zp, ip) - DN(J, zm, im);
-      if (vx) S[J][0] += (W * CT(vx)) * d;
-      if (vy) S[J][1] += (W * CT(vy)) * d;
-      if (vz) S[J][2] += (W * CT(vz)) * d;
-      if (a.self_on) {
-        const CT e = PS(J, zp, ip) - PS(J, zm, im);
-        if (vx) T[J][0] += (W * CT(vx)) * e;
-        if (vy) T[J][1] += (W * CT(vy)) * e;
-        if (vz) T[J][2] += (W * CT(vz)) * e;
-      }
+    const int zp = sl[HZ + vz] * PLANE, zm = sl[HZ - vz] * PLANE;
+    const P2<CT> d = psub(s_dn[zp + ip], s_dn[zm + im]);
+    if (vx) S[0] = pfma(pbc(CT(SN::W(k) * vx)), d, S[0]);
+    if (vy) S[1] = pfma(pbc(CT(SN::W(k) * vy)), d, S[1]);
+    if (vz) S[2] = pfma(pbc(CT(SN::W(k) * vz)), d, S[2]);
+    if (a.self_on) {
+      const P2<CT> e = psub(s_psi[zp + ip], s_psi[zm + im]);
+      if (vx) T[0] = pfma(pbc(CT(SN::W(k) * vx)), e, T[0]);
+      if (vy) T[1] = pfma(pbc(CT(SN::W(k) * vy)), e, T[1]);
+      if (vz) T[2] = pfma(pbc(CT(SN::W(k) * vz)), e, T[2]);
     }
   }
-  CT F[2][3], j[2][3];
+  // cross term: component A feels the gradient of n_B and vice versa
+  const P2<CT> cn = pmul(pbc(a.gcross), n), cp = pmul(a.gself, psi);
 #pragma unroll
-  for (int J = 0; J < 2; ++J) {
+  for (int m = 0; m < 3; ++m) F[m] = pfma(cp, T[m], pmul(cn, pswap(S[m])));
+}
+
+// Half momenta h_J = j_J + F_J / 2 with j_J = sum_i g_i xi_i from opposite-pair differences.
+template <int LAT, class CT>
+__device__ __forceinline__ void half_momentum(const P2<CT> (&g)[Lattice<LAT>::Q], const P2<CT> (&F)[3],
+                                              P2<CT> (&h)[3]) {
+  using L = Lattice<LAT>;
+  constexpr int Q = L::Q;
+  P2<CT> d[Q];
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) d[i] = psub(g[i], g[i + 1]);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    P2<CT> acc = pbc(CT(0));
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+      const int cm = L::c(i, m);
+      if (cm > 0) acc = padd(acc, d[i]);
+      if (cm < 0) acc = psub(acc, d[i]);
+    }
+    h[m] = pfma(pbc(CT(0.5)), F[m], acc);
+  }
+}
+
+// Common velocity of Eq. u: n u = h_A + h_B.
+template <class CT>
+__device__ __forceinline__ void common_velocity(const P2<CT> (&h)[3], P2<CT> n, CT (&u)[3]) {
+  const CT inv_n = rdiv(CT(1), radd(n.x, n.y));
+#pragma unroll
+  for (int m = 0; m < 3; ++m) u[m] = rmul(radd(h[m].x, h[m].y), inv_n);
+}
+
+// BGK + Guo in pair form.  With omega = 1/tau, gamma = 1 - 1/(2 tau):
+//   f* = (1 - omega) f + omega f^eq + gamma F_i
+//      = (1 - omega) f + w_i [a0 + a2 cu^2 + a3 cu cF  +/-  (a1 cu + a4 cF)]
+// with cu = xi.u, cF = xi.F for the "+" member of an opposite pair and
+//   a0 = omega dn - 1.5 omega n u.u - 3 gamma u.F, a1 = 3 omega n,
+//   a2 = 4.5 omega n, a3 = 9 gamma, a4 = 3 gamma
+// (Eq. feq with c_s^2 = 1/3 written as a deviation from w_i nbar, and Eq. Guo).
+template <int LAT, class CT>
+__device__ __forceinline__ void collide_pair(const StepArgs<CT> &a, const P2<CT> (&g)[Lattice<LAT>::Q], P2<CT> n,
+                                             P2<CT> dn, const CT (&u)[3], const P2<CT> (&F)[3],
+                                             P2<CT> (&out)[Lattice<LAT>::Q]) {
+  using L = Lattice<LAT>;
+  constexpr int Q = L::Q;
+  const P2<CT> om = a.omega, ga = a.guo;
+  const CT uu = rfma(u[2], u[2], rfma(u[1], u[1], rmul(u[0], u[0])));
+  const P2<CT> uF = pfma(pbc(u[2]), F[2], pfma(pbc(u[1]), F[1], pmul(pbc(u[0]), F[0])));
+  const P2<CT> a0 =
+      pfma(pmul(pbc(CT(-3)), ga), uF, pfma(pmul(pmul(pbc(CT(-1.5)), om), n), pbc(uu), pmul(om, dn)));
+  const P2<CT> a1 = pmul(pmul(pbc(CT(3)), om), n), a2 = pmul(pmul(pbc(CT(4.5)), om), n);
+  const P2<CT> a3 = pmul(pbc(CT(9)), ga), a4 = pmul(pbc(CT(3)), ga);
+  const P2<CT> keep = psub(pbc(CT(1)), om);
+  out[0] = pfma(keep, g[0], pmul(pbc(CT(L::w(0))), a0));
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    const int c[3] = {L::c(i, 0), L::c(i, 1), L::c(i, 2)};
+    const P2<CT> w = pbc(CT(L::w(i)));
+    CT cu = CT(0);
+    P2<CT> cF = pbc(CT(0));
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-      F[J][m] = a.gcross * n[J] * S[1 - J][m] + a.gself[J] * psi[J] * T[J][m];
-      CT acc = CT(0);
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const int cm = L::c(i, m);
-        if (cm > 0) acc += g[J][i];
-        if (cm < 0) acc -= g[J][i];
-      }
-      j[J][m] = acc;
+      if (c[m] > 0) { cu = radd(cu, u[m]); cF = padd(cF, F[m]); }
+      if (c[m] < 0) { cu = rsub(cu, u[m]); cF = psub(cF, F[m]); }
     }
+    const P2<CT> cu2 = pbc(cu);
+    const P2<CT> E = pfma(cu2, pfma(pmul(w, a2), cu2, pmul(pmul(w, a3), cF)), pmul(w, a0));
+    const P2<CT> O = pfma(pmul(w, a1), cu2, pmul(pmul(w, a4), cF));
+    out[i] = pfma(keep, g[i], padd(E, O));
+    out[i + 1] = pfma(keep, g[i + 1], psub(E, O));
   }
+}
+
+// Status: a non-finite density, or a non-positive one while psi = exp(-1/n) is in use.
+template <class CT>
+__device__ __forceinline__ void check_density(const StepArgs<CT> &a, P2<CT> n) {
+  const bool finite = fabs(n.x + n.y) < CT(INFINITY);
+  const bool positive = n.x > CT(0) && n.y > CT(0);
+  if (!finite || (a.self_on && a.psi_exp && !positive)) atomicOr(a.err, 1u);
+}
+
+template <class ST, class CT, int Q>
+__device__ __forceinline__ void store_pairs(const StepArgs<CT> &a, ST *__restrict__ dst, int64_t site,
+                                            const P2<CT> (&out)[Q]) {
+#pragma unroll
+  for (int i = 0; i < Q; ++i) Codec2<ST, CT>::store(dst + ((int64_t)i * a.N + site) * 2, out[i], a.scale[i]);
+}
+
+// Collision of one site from its arriving population pairs g[i] and the ring.
+template <int LAT, int STEN, class ST, class CT, int TY>
+__device__ __forceinline__ void collide_site(const StepArgs<CT> &a, const P2<CT> (&g)[Lattice<LAT>::Q],
+                                             const P2<CT> *s_dn, const P2<CT> *s_psi, const int *sl, int own,
+                                             bool valid, ST *__restrict__ dst, int64_t site) {
+  constexpr int Q = Lattice<LAT>::Q;
+  constexpr int HZ = (LAT == kD3Q19) ? Stencil<LAT, STEN>::HALO : 0;
+  constexpr int H = Stencil<LAT, STEN>::HALO;
+  constexpr int PLANE = (32 + 2 * H) * (TY + 2 * H);
+  const P2<CT> dn = s_dn[sl[HZ] * PLANE + own];
+  const P2<CT> n = padd(a.nbar, dn);
+  const P2<CT> psi = a.self_on ? padd(a.psibar, s_psi[sl[HZ] * PLANE + own]) : pbc(CT(0));
+  P2<CT> F[3], h[3], out[Q];
   CT u[3];
-  const CT inv_n = CT(1) / (n[0] + n[1]);
-#pragma unroll
-  for (int m = 0; m < 3; ++m) u[m] = ((j[0][m] + CT(0.5) * F[0][m]) + (j[1][m] + CT(0.5) * F[1][m])) * inv_n;
-  const CT uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-  if (valid && !(n[0] > CT(0) && n[1] > CT(0))) atomicOr(a.err, 1u);
-#pragma unroll
-  for (int J = 0; J < 2; ++J) {
-    const CT uF = u[0] * F[J][0] + u[1] * F[J][1] + u[2] * F[J][2];
-    ST *out = dst + (int64_t)J * Q * N + site;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
-      const CT w = CT(L::w(i));
-      const CT cu = CT(cx) * u[0] + CT(cy) * u[1] + CT(cz) * u[2];
-      const CT cF = CT(cx) * F[J][0] + CT(cy) * F[J][1] + CT(cz) * F[J][2];
-      // deviation of Eq. feq from w_i nbar_J, and the Guo term
-      const CT geq = w * (dn[J] + n[J] * (CT(3) * cu + CT(4.5) * cu * cu - CT(1.5) * uu));
-      const CT Fi = w * (CT(3) * cF + CT(9) * cu * cF - CT(3) * uF);
-      const CT gout = g[J][i] - a.omega[J] * (g[J][i] - geq) + a.guo[J] * Fi;
-      if (valid) Codec<ST, CT>::store(out + (int64_t)i * N, gout, a.scale[J][i]);
-    }
+  force_pair<LAT, STEN, CT, TY>(a, s_dn, s_psi, sl, own, n, psi, F);
+  half_momentum<LAT, CT>(g, F, h);
+  common_velocity<CT>(h, n, u);
+  collide_pair<LAT, CT>(a, g, n, dn, u, F, out);
+  if (valid) {
+    check_density<CT>(a, n);
+    store_pairs<ST, CT, Q>(a, dst, site, out);
   }
 }
 
@@ -169,9 +231,9 @@ __global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 16 / TY)) sc_step_ker
   constexpr int NT = 32 * TY;
   constexpr bool KEEP = (HZ <= 1);  // own populations stay in registers until collided
 
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  CT *s_dn = reinterpret_cast<CT *>(smem_raw);  // [2][NPL][PLANE]
-  CT *s_psi = s_dn + 2 * NPL * PLANE;           // [2][NPL][PLANE]
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  P2<CT> *s_dn = reinterpret_cast<P2<CT> *>(smem_raw);  // [NPL][PLANE]
+  P2<CT> *s_psi = s_dn + NPL * PLANE;                   // [NPL][PLANE]
 
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -185,20 +247,18 @@ __global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 16 / TY)) sc_step_ker
   const int gx = (x0 + tx) % nx, gy = (y0 + ty) % ny;
   const int own = (ty + H) * SX + (tx + H);
 
-  CT cur[2][Q], nxt[2][Q];
+  P2<CT> cur[Q], nxt[Q];
   int slot = 0;
   for (int p = z0 - HZ; p <= zend - 1 + HZ; ++p) {
     const int gz = ((p % nz) + nz) % nz;
     // ---- density / psi deviations of this plane: own site
-#pragma unroll
-    for (int J = 0; J < 2; ++J) {
-      const CT dn = pull_site<LAT, ST, CT, KEEP>(src, J, gx, gy, gz, nx, ny, nz, N, a.inv_scale[J], nxt[J]);
-      s_dn[(J * NPL + slot) * PLANE + own] = dn;
-      if (a.self_on) s_psi[(J * NPL + slot) * PLANE + own] = psi_deviation(dn, a.nbar[J], a.psibar[J], a.psi_exp);
+    {
+      const P2<CT> dn = pull_site<LAT, ST, CT, KEEP>(src, gx, gy, gz, nx, ny, nz, N, a.inv_scale, nxt);
+      s_dn[slot * PLANE + own] = dn;
+      if (a.self_on) s_psi[slot * PLANE + own] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp);
     }
     // ---- halo sites (full rows first, for coalescing, then the side columns)
-    for (int t = tid; t < 2 * NHALO; t += NT) {
-      const int J = t / NHALO, h = t - J * NHALO;
+    for (int h = tid; h < NHALO; h += NT) {
       int px, py;
       if (h < 2 * H * SX) {
         const int r = h / SX;
@@ -210,10 +270,10 @@ __global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 16 / TY)) sc_step_ker
         px = c < H ? c - H : 32 + (c - H);
       }
       const int hx = ((x0 + px) % nx + nx) % nx, hy = ((y0 + py) % ny + ny) % ny;
-      const CT dn = pull_site<LAT, ST, CT, false>(src, J, hx, hy, gz, nx, ny, nz, N, a.inv_scale[J], nullptr);
+      const P2<CT> dn = pull_site<LAT, ST, CT, false>(src, hx, hy, gz, nx, ny, nz, N, a.inv_scale, nullptr);
       const int idx = (py + H) * SX + (px + H);
-      s_dn[(J * NPL + slot) * PLANE + idx] = dn;
-      if (a.self_on) s_psi[(J * NPL + slot) * PLANE + idx] = psi_deviation(dn, a.nbar[J], a.psibar[J], a.psi_exp);
+      s_dn[slot * PLANE + idx] = dn;
+      if (a.self_on) s_psi[slot * PLANE + idx] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp);
     }
     __syncthreads();
 
@@ -228,19 +288,13 @@ __global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 16 / TY)) sc_step_ker
       if (HZ == 1) {
         collide_site<LAT, STEN, ST, CT, TY>(a, cur, s_dn, s_psi, sl, own, valid_xy, dst, site);
       } else {
-        if (!KEEP) {
-#pragma unroll
-          for (int J = 0; J < 2; ++J)
-            pull_site<LAT, ST, CT, true>(src, J, gx, gy, gzc, nx, ny, nz, N, a.inv_scale[J], nxt[J]);
-        }
+        if (!KEEP) pull_site<LAT, ST, CT, true>(src, gx, gy, gzc, nx, ny, nz, N, a.inv_scale, nxt);
         collide_site<LAT, STEN, ST, CT, TY>(a, nxt, s_dn, s_psi, sl, own, valid_xy, dst, site);
       }
     }
     if (HZ == 1) {
 #pragma unroll
-      for (int J = 0; J < 2; ++J)
-#pragma unroll
-        for (int i = 0; i < Q; ++i) cur[J][i] = nxt[J][i];
+      for (int i = 0; i < Q; ++i) cur[i] = nxt[i];
     }
     slot = (slot + 1 == NPL) ? 0 : slot + 1;
   }
