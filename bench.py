@@ -31,6 +31,12 @@ RADIUS = 24.0
 G_CROSS = 3.6  # G c_s^2 = 1.2: the largest tested coupling that is stable in three dimensions at tau = 1
 INNER = 2048  # time steps per benchmark step (section 4: delta t = 2^11); --inner overrides for profiling
 BYTES_PER_SITE = {"f32": 304, "f16": 152, "bf16": 152, "f64": 608}  # 2 comps x 19 pops x (read + write) x bytes
+# DRAM bytes (read + write) of one step launch on this workload, from an ncu capture
+# (profiles/sc_step_staged_d3q19_128cube.md); reported only while the kernel sources
+# still hash to the captured version.
+KERNEL_SOURCES = ["paper_2112_02574_gb300/csrc/sc_common.cuh", "paper_2112_02574_gb300/csrc/sc_step_kernel.cuh",
+                  "paper_2112_02574_gb300/csrc/sc_step_staged.cuh"]
+MEASURED_TRAFFIC = {("aac010c37336a0b0", "f32"): 624.268032e6}
 
 
 def workload_config(storage: str):
@@ -106,6 +112,16 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def kernel_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def measured_peak():
@@ -282,7 +298,9 @@ def run_gpu(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": storage, "data": "synthetic", "config": workload_config(storage),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "sc_step_kernel", "bytes_per_site": BYTES_PER_SITE[storage],
+                     "traffic": MEASURED_TRAFFIC.get((kernel_hash(), storage)) if args.variant != 1 else None,
+                     "kernel": "sc_step_staged" if args.variant != 1 else "sc_step_kernel",
+                     "bytes_per_site": BYTES_PER_SITE[storage], "algorithmic_bytes_per_launch": alg_bytes,
                      "kernel_ms": kern_ms, "peak_source": peak_kind},
         "hbm_roofline_mlups_frac": value / world * 1e6 * BYTES_PER_SITE[storage] / (peak * 1e9),
         "gpu_launches": launches, "clocks": clk.summary(), "e2e": e2e,
