@@ -154,6 +154,29 @@ sc_status sc_bulk_pressure_at(sc_ctx *ctx, const int32_t node[3], double *out);
 sc_status sc_sigma_minimum(const double *rows, int32_t nbins, const double *P_in_out, int32_t dim, double R_lo,
                            double R_hi, double R_step, double *out, void *stream);
 
+/* Pressure-tensor profile without any device allocation.  The paper has no
+ * counterpart to this entry point; it exists for callers that cannot allocate
+ * device memory at the point of the call -- for instance code that has handed
+ * all device memory to its own pool allocator, or that runs where the implicit
+ * device synchronisation of cudaMalloc / cudaFree is not allowed.  It computes
+ * the same rows as sc_pressure_profile (same kinds, same layout of out), but
+ * from caller-provided density fields nA, nB (device FP64 [N], N from params;
+ * params gives the lattice, stencil, psi_self, G and G_self) with the
+ * pseudopotential evaluated on the fly, and without a context or workspace.
+ * Its only scratch is a fixed 4 MiB __device__ array inside this library, which
+ * every GPU that loads the library holds until the process exits; nbins may be
+ * at most 4096 (larger requests return SC_EINVAL).  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.  The first call on a device looks up
+ * the array's device address (once per device, with that device current); make
+ * that first call before any stream capture.  All calls share the array and
+ * each call overwrites every entry it later reads, so nothing needs clearing;
+ * calls that overlap on the GPU (other streams, other host threads) race on
+ * it.  out: device FP64 [nbins][6].  stream: cudaStream_t as void*.
+ * Asynchronous. */
+sc_status sc_pressure_profile_noalloc(const sc_params *params, const double *nA, const double *nB, int32_t kind,
+                                      const double centre[3], double bin_width, int32_t nbins, double *out,
+                                      void *stream);
+
 /* Conserved totals, FP64, deterministic: out device [5] = (mass_A, mass_B,
  * momentum x, y, z) summed over the lattice (section 2).  Asynchronous. */
 sc_status sc_totals(sc_ctx *ctx, double *out);

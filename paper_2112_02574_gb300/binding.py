@@ -70,6 +70,7 @@ def _load():
         "sc_pressure_profile": (I32, [V, I32, ctypes.POINTER(D), D, I32, V]),
         "sc_bulk_pressure_at": (I32, [V, ctypes.POINTER(I32), V]),
         "sc_sigma_minimum": (I32, [V, I32, V, I32, D, D, D, V, V]),
+        "sc_pressure_profile_noalloc": (I32, [P, V, V, I32, ctypes.POINTER(D), D, I32, V, V]),
         "sc_totals": (I32, [V, V]),
         "sc_sync": (I32, [V]),
         "sc_run_host": (I32, [P, V, V, I64, V, V, V, Z, V]),
@@ -156,6 +157,13 @@ def sc_set_state(ctx, src):
 def sc_pressure_profile(ctx, kind, centre, bin_width, nbins, out):
     c = (ctypes.c_double * 3)(*[float(v) for v in centre])
     _check(lib.sc_pressure_profile(ctx, int(kind), c, float(bin_width), int(nbins), _ptr(out)))
+
+
+def sc_pressure_profile_noalloc(params, nA, nB, kind, centre, bin_width, nbins, out, stream=None):
+    """Profile from device density fields with no device allocation (see include/sc.h)."""
+    c = (ctypes.c_double * 3)(*[float(v) for v in centre])
+    _check(lib.sc_pressure_profile_noalloc(ctypes.byref(params), _ptr(nA), _ptr(nB), int(kind), c,
+                                           float(bin_width), int(nbins), _ptr(out), _stream_ptr(stream)))
 
 
 def sc_bulk_pressure_at(ctx, node, out):

@@ -11,6 +11,10 @@
 #include "sc_aux.cuh"
 #include "sc_dispatch.h"
 
+namespace scgb {
+sc_status set_error(sc_status st, const char *msg);
+}
+
 using namespace scgb;
 
 namespace {
@@ -123,6 +127,10 @@ int default_tile_z(const sc_params *p) {
 }
 
 }  // namespace
+
+// Records the calling thread's sc_last_error() message for entry points defined
+// in other translation units of the library.
+sc_status scgb::set_error(sc_status st, const char *msg) { return fail(st, "%s", msg); }
 
 struct sc_ctx {
   sc_params p;
