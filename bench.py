@@ -153,6 +153,37 @@ def cpu_baseline(budget_s: float = 12.0, shape=(64, 64, 64)):
                       f"{RADIUS * shape[0] / SHAPE[0]:g}), {dt:.1f} s"}
 
 
+PRECISION_STEPS = 4096  # two convergence-check intervals of the bench workload
+
+
+def surface_of_tension_after(B, storage_code, steps, dev, stream):
+    """(dP, R_s, sigma_s) of the bench droplet after `steps` fused steps in one storage mode."""
+    params = B.make_params(SHAPE, lattice=B.SC_D3Q19, stencil=B.SC_FORCE_E4, psi_self=B.SC_PSI_EXP,
+                           storage=storage_code, tau=(1.0, 1.0), G=G_CROSS, G_self=(0.0, 0.0))
+    nA0, nB0 = fields()
+    import torch
+
+    with torch.cuda.stream(stream):
+        sim = B.Simulation(params, nA0, nB0, device=dev, stream=stream)
+        sim.step(steps)
+        _, out = B.surface_of_tension(sim, (64.0, 64.0, 64.0), 0.5, nbins=128)
+        B.sc_sync(sim.ctx)
+        o = out.cpu().numpy()
+    return {"dP": float(o[0]), "Rs": float(o[2]), "sigma_s": float(o[3])}
+
+
+def precision_block(B, storages, dev, stream):
+    """Errors of dP, R_s and sigma_s against the FP64-storage path (itself within 1e-13 per step of the
+    FP64 CPU oracle) after PRECISION_STEPS steps of the bench workload."""
+    ref = surface_of_tension_after(B, B.SC_STORE_F64, PRECISION_STEPS, dev, stream)
+    out = {"steps": PRECISION_STEPS, "reference": "FP64-storage GPU path", "reference_values": ref}
+    codes = {"f32": B.SC_STORE_F32, "f16": B.SC_STORE_F16, "bf16": B.SC_STORE_BF16}
+    for st in storages:
+        got = surface_of_tension_after(B, codes[st], PRECISION_STEPS, dev, stream)
+        out[st] = {k + "_rel_err": abs(got[k] - ref[k]) / abs(ref[k]) for k in ("dP", "Rs", "sigma_s")}
+    return out
+
+
 def run_reference(args, rank, world):
     """The oracle arm: rank 0 only, FP64 on the host cores, same metric and unit."""
     if rank != 0:
@@ -291,6 +322,19 @@ def run_gpu(args, rank, world, local_rank):
                "h2d_bytes_per_step": 2 * sites * 8, "d2h_bytes_per_step": 2 * sites * 8,
                "note": f"sc_run_host per step: H2D of n_A0, n_B0 (FP64), create, {INNER} steps, D2H of n_A, n_B"}
 
+    precision = None
+    if not args.no_precision and rank == 0:
+        others = [st for st in ("f32", "f16") if st != storage]
+        precision = precision_block(B, [storage] + others, dev, stream)
+        # the other storage mode's throughput, measured like `value` (same steps, same workload)
+        if "f16" in others or "f32" in others:
+            alt = others[0]
+            precision["throughput"] = {alt: alt_throughput(B, alt, args, dev, stream)}
+
+    batch = None
+    if not args.no_batch and rank == 0:
+        batch = batch_block(B, dev, stream)
+
     if rank != 0:
         return
     line = {
@@ -303,12 +347,84 @@ def run_gpu(args, rank, world, local_rank):
                      "bytes_per_site": BYTES_PER_SITE[storage], "algorithmic_bytes_per_launch": alg_bytes,
                      "kernel_ms": kern_ms, "peak_source": peak_kind},
         "hbm_roofline_mlups_frac": value / world * 1e6 * BYTES_PER_SITE[storage] / (peak * 1e9),
-        "gpu_launches": launches, "clocks": clk.summary(), "e2e": e2e,
+        "gpu_launches": launches, "clocks": clk.summary(), "e2e": e2e, "precision": precision,
+        "batch_sweep": batch,
         "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(line), flush=True)
+
+
+def sweep_droplets():
+    """The batched radius sweep: 16 droplets, R_k = 8 + 32 k / 15, cubes of odd side 2 floor(2R) + 1
+    (about 4R, centre on a node), even k symmetric, odd k asymmetric (G_AA c_s^2 = -0.2)."""
+    import sc_synth
+
+    out = []
+    for k in range(16):
+        R = 8.0 + 32.0 * k / 15.0
+        L = 2 * int(2 * R) + 1
+        G_self = (0.0, 0.0) if k % 2 == 0 else (-0.6, 0.0)
+        f = sc_synth.droplet((L, L, L), (L // 2,) * 3, R, n_in=0.95, n_out=0.05, amplitude=1e-3,
+                             seed=20211206 + 3 + k)
+        out.append((L, R, G_self, f))
+    return out
+
+
+def batch_block(B, dev, stream, steps=128):
+    """Throughput of the batched radius sweep (one launch per step, CUDA graph), FP32 and FP16 storage;
+    tile rows chosen by the autotuner."""
+    import torch
+
+    from paper_2112_02574_gb300 import tune
+
+    drops = sweep_droplets()
+    sites = sum(L ** 3 for L, _, _, _ in drops)
+    res = {"lattices": len(drops), "sites": sites, "sides": [L for L, _, _, _ in drops]}
+    for name, code in (("f32", B.SC_STORE_F32), ("f16", B.SC_STORE_F16)):
+        plist = [B.make_params((L, L, L), lattice=B.SC_D3Q19, psi_self=B.SC_PSI_EXP, storage=code, G=G_CROSS,
+                               G_self=gs, tile_z=16) for L, _, gs, _ in drops]
+        fields_ = [f for _, _, _, f in drops]
+        ty, _, table = tune.tune_batch_tile_y(plist, fields_, steps=16, device=dev)
+        plist = [B.make_params((L, L, L), lattice=B.SC_D3Q19, psi_self=B.SC_PSI_EXP, storage=code, G=G_CROSS,
+                               G_self=gs, tile_z=16, tile_y=ty) for L, _, gs, _ in drops]
+        with torch.cuda.stream(stream):
+            batch = B.Batch(plist, fields_, device=dev, stream=stream)
+            batch.step(64)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            batch.step(steps)
+            b.record(stream)
+            b.synchronize()
+        ms = a.elapsed_time(b)
+        res[name] = {"MLUPS": sites * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps, "tile_y": ty,
+                     "tuning": [[t, round(m, 4)] for t, m in table]}
+        del batch
+    return res
+
+
+def alt_throughput(B, storage, args, dev, stream):
+    """MLUPS of the fused step alone in another storage mode (same workload, same timing rules)."""
+    import torch
+
+    code = {"f32": B.SC_STORE_F32, "f16": B.SC_STORE_F16, "bf16": B.SC_STORE_BF16}[storage]
+    params = B.make_params(SHAPE, lattice=B.SC_D3Q19, stencil=B.SC_FORCE_E4, psi_self=B.SC_PSI_EXP, storage=code,
+                           tau=(1.0, 1.0), G=G_CROSS, G_self=(0.0, 0.0))
+    nA0, nB0 = fields()
+    with torch.cuda.stream(stream):
+        sim = B.Simulation(params, nA0, nB0, device=dev, stream=stream)
+        B.sc_step(sim.ctx, 3 * INNER // 4)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        B.sc_step(sim.ctx, INNER)
+        b.record(stream)
+        b.synchronize()
+        B.sc_sync(sim.ctx)
+    ms = a.elapsed_time(b)
+    sites = SHAPE[0] * SHAPE[1] * SHAPE[2]
+    return {"MLUPS": sites * INNER / (ms * 1e-3) / 1e6, "kernel_ms": ms / INNER,
+            "hbm_frac": sites * BYTES_PER_SITE[storage] / (ms / INNER * 1e-3) / 1e9 / measured_peak()[0]}
 
 
 def main():
@@ -325,6 +441,8 @@ def main():
     ap.add_argument("--kernel-events", action="store_true", help="record per-step kernel events in the timed loop")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-precision", action="store_true", help="skip the sigma / R_s / dP error block")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched radius sweep block")
     ap.add_argument("--inner", type=int, default=INNER, help="time steps per benchmark step (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()

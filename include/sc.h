@@ -191,6 +191,29 @@ sc_status sc_sync(sc_ctx *ctx);
 sc_status sc_run_host(const sc_params *params, const double *nA0, const double *nB0, int64_t nsteps, double *nA,
                       double *nB, void *workspace, size_t ws_bytes, void *stream);
 
+/* ---- batches: several lattices stepped by one kernel launch per step ----
+ * The batched radius sweep: lattices of different sizes and parameters (same
+ * lattice type, stencil, storage and tile_y) stepped together; every time step
+ * is ONE launch of the generic step kernel over a work list of (lattice, tile)
+ * items, replayed from a CUDA graph of 32 chained launches (built explicitly,
+ * no stream capture).  Each member is an ordinary context for the analysis
+ * entry points (sc_moments, sc_pressure_profile, sc_bulk_pressure_at, ...);
+ * sc_step refuses batch members. */
+typedef struct sc_batch sc_batch;
+/* Device workspace for n lattices (0 if the parameters are invalid). */
+size_t sc_batch_workspace_bytes(int32_t n, const sc_params *params);
+/* params[n]; nA0[k], nB0[k]: device FP64 [N_k] initial densities of lattice k.
+ * Synchronises the stream once (initialisation and table upload). */
+sc_status sc_batch_create(int32_t n, const sc_params *params, const double *const *nA0, const double *const *nB0,
+                          void *workspace, size_t ws_bytes, void *stream, sc_batch **out);
+/* Advance every member by nsteps time steps (section 2); asynchronous. */
+sc_status sc_batch_step(sc_batch *batch, int64_t nsteps);
+/* Member k as a context (owned by the batch; NULL if k is out of range). */
+sc_ctx *sc_batch_member(sc_batch *batch, int32_t k);
+/* Batched step launches issued so far (each steps every member once). */
+int64_t sc_batch_launches(const sc_batch *batch);
+void sc_batch_destroy(sc_batch *batch);
+
 /* Number of step-kernel launches issued by this context so far. */
 int64_t sc_kernel_launches(const sc_ctx *ctx);
 

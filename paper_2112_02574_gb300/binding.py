@@ -75,6 +75,12 @@ def _load():
         "sc_sync": (I32, [V]),
         "sc_run_host": (I32, [P, V, V, I64, V, V, V, Z, V]),
         "sc_kernel_launches": (I64, [V]),
+        "sc_batch_workspace_bytes": (Z, [I32, P]),
+        "sc_batch_create": (I32, [I32, P, ctypes.POINTER(V), ctypes.POINTER(V), V, Z, V, ctypes.POINTER(V)]),
+        "sc_batch_step": (I32, [V, I64]),
+        "sc_batch_member": (V, [V, I32]),
+        "sc_batch_launches": (I64, [V]),
+        "sc_batch_destroy": (None, [V]),
         "sc_reference_density": (I32, [V, ctypes.POINTER(D)]),
         "sc_destroy": (None, [V]),
         "sc_last_error": (ctypes.c_char_p, []),
@@ -192,6 +198,41 @@ def sc_run_host(params, nA0, nB0, nsteps, nA, nB, workspace, stream=None):
                            _ptr(workspace), workspace.numel(), _stream_ptr(stream)))
 
 
+def sc_batch_workspace_bytes(params_list) -> int:
+    arr = (sc_params * len(params_list))(*params_list)
+    return lib.sc_batch_workspace_bytes(len(params_list), arr)
+
+
+def sc_batch_create(params_list, nA0_list, nB0_list, workspace, stream=None):
+    n = len(params_list)
+    arr = (sc_params * n)(*params_list)
+    a = (ctypes.c_void_p * n)(*[t.data_ptr() for t in nA0_list])
+    b = (ctypes.c_void_p * n)(*[t.data_ptr() for t in nB0_list])
+    out = ctypes.c_void_p()
+    _check(lib.sc_batch_create(n, arr, a, b, _ptr(workspace), workspace.numel(), _stream_ptr(stream),
+                               ctypes.byref(out)))
+    return out
+
+
+def sc_batch_step(batch, nsteps: int):
+    _check(lib.sc_batch_step(batch, int(nsteps)))
+
+
+def sc_batch_member(batch, k: int):
+    ctx = lib.sc_batch_member(batch, int(k))
+    if not ctx:
+        raise ScError(SC_EINVAL, sc_last_error())
+    return ctypes.c_void_p(ctx)
+
+
+def sc_batch_launches(batch) -> int:
+    return lib.sc_batch_launches(batch)
+
+
+def sc_batch_destroy(batch):
+    lib.sc_batch_destroy(batch)
+
+
 def sc_kernel_launches(ctx) -> int:
     return lib.sc_kernel_launches(ctx)
 
@@ -291,6 +332,54 @@ class Simulation:
     @property
     def nbar(self):
         return sc_reference_density(self.ctx)
+
+
+class _Member(Simulation):
+    """A batch member viewed as a Simulation (no own workspace; the batch owns the context)."""
+
+    def __init__(self, batch, k, params, device):
+        self.params = params
+        self.shape = (params.nx, params.ny, params.nz)
+        self.N = params.nx * params.ny * params.nz
+        self.Q = 19 if params.lattice == SC_D3Q19 else 9
+        self.device = device
+        self.stream = batch.stream
+        self._batch = batch  # keeps the batch (and its workspace) alive
+        self.ctx = sc_batch_member(batch.handle, k)
+
+    def __del__(self):
+        pass  # the batch owns the context
+
+
+class Batch:
+    """Several lattices stepped together: one kernel launch per time step."""
+
+    def __init__(self, params_list, fields, device="cuda", stream=None):
+        self.params = list(params_list)
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        ws = sc_batch_workspace_bytes(self.params)
+        if ws == 0:
+            raise ScError(SC_EINVAL, sc_last_error())
+        self.workspace = torch.empty(ws, dtype=torch.uint8, device=self.device)
+        a = [torch.as_tensor(f[0], dtype=torch.float64).reshape(-1).to(self.device).contiguous() for f in fields]
+        b = [torch.as_tensor(f[1], dtype=torch.float64).reshape(-1).to(self.device).contiguous() for f in fields]
+        torch.cuda.synchronize(self.device)
+        self.handle = sc_batch_create(self.params, a, b, self.workspace, self.stream)
+        self.members = [_Member(self, k, p, self.device) for k, p in enumerate(self.params)]
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            sc_batch_destroy(h)
+            self.handle = None
+
+    def step(self, n: int = 1):
+        sc_batch_step(self.handle, n)
+
+    @property
+    def launches(self) -> int:
+        return sc_batch_launches(self.handle)
 
 
 def surface_of_tension(sim: Simulation, centre, bin_width=0.5, nbins=None, in_node=None, out_node=None,

@@ -147,6 +147,22 @@ struct sc_ctx {
   int64_t launches;
   int64_t steps;
   int64_t fields_at;  // step count the FP64 fields were computed at (-1: stale)
+  int in_batch;       // stepped by a batch (sc_step refuses)
+};
+
+struct sc_batch {
+  int n;
+  sc_ctx **ctx;
+  cudaStream_t stream;
+  void *args_dev;     // StepArgs<CT>[n] (parity 0: buffer 0 -> buffer 1)
+  int4 *items_dev;    // (lattice, bx, by, bz) per block
+  int nitems;
+  int tile_y;
+  const void *kernel;
+  size_t smem;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  int64_t steps, launches;
 };
 
 namespace {
@@ -399,6 +415,7 @@ sc_status sc_create(const sc_params *params, const double *nA0, const double *nB
 
 sc_status sc_step(sc_ctx *c, int64_t nsteps) {
   if (!c) return fail(SC_EINVAL, "ctx is NULL");
+  if (c->in_batch) return fail(SC_EINVAL, "this context belongs to a batch: step it with sc_batch_step");
   if (nsteps < 0) return fail(SC_EINVAL, "nsteps must be >= 0");
   for (int64_t t = 0; t < nsteps; ++t) {
     sc_status st = launch_one_step(c);
@@ -591,6 +608,221 @@ sc_status sc_run_host(const sc_params *params, const double *nA0, const double *
   if (st == SC_OK) st = sc_sync(c);
   sc_destroy(c);
   return st;
+}
+
+// ------------------------------------------------------------------ batches
+namespace {
+constexpr int kGraphSteps = 32;  // steps per graph replay (even: parity preserved)
+
+size_t batch_table_bytes(int32_t n, const sc_params *params, int *nitems_out) {
+  int nitems = 0;
+  for (int k = 0; k < n; ++k) {
+    const sc_params &p = params[k];
+    const int ty = p.tile_y ? p.tile_y : (p.lattice == SC_D3Q19 ? 8 : 4);
+    const int tz = p.lattice == SC_D2Q9 ? 1 : (p.tile_z ? (p.tile_z < p.nz ? p.tile_z : p.nz) : (p.nz < 32 ? p.nz : 32));
+    nitems += ((p.nx + 31) / 32) * ((p.ny + ty - 1) / ty) * ((p.nz + tz - 1) / tz);
+  }
+  if (nitems_out) *nitems_out = nitems;
+  return align_up(sizeof(StepArgs<double>) * (size_t)n) + align_up(sizeof(int4) * (size_t)nitems);
+}
+
+sc_status batch_validate(int32_t n, const sc_params *params) {
+  if (n < 1 || n > 4096) return fail(SC_EINVAL, "a batch holds 1 to 4096 lattices");
+  if (!params) return fail(SC_EINVAL, "params is NULL");
+  for (int k = 0; k < n; ++k) {
+    sc_status st = validate(&params[k]);
+    if (st != SC_OK) return st;
+    const sc_params &a = params[0], &b = params[k];
+    const int tya = a.tile_y ? a.tile_y : (a.lattice == SC_D3Q19 ? 8 : 4);
+    const int tyb = b.tile_y ? b.tile_y : (b.lattice == SC_D3Q19 ? 8 : 4);
+    if (a.lattice != b.lattice || a.stencil != b.stencil || a.storage != b.storage || tya != tyb)
+      return fail(SC_EINVAL, "all lattices of a batch share lattice, stencil, storage and tile_y");
+    if (b.variant == 2) return fail(SC_EINVAL, "a batch steps with the generic kernel (variant 0 or 1)");
+  }
+  return SC_OK;
+}
+}  // namespace
+
+size_t sc_batch_workspace_bytes(int32_t n, const sc_params *params) {
+  if (batch_validate(n, params) != SC_OK) return 0;
+  size_t total = 0;
+  for (int k = 0; k < n; ++k) total += layout_of(&params[k]).total;
+  return total + batch_table_bytes(n, params, nullptr);
+}
+
+sc_status sc_batch_create(int32_t n, const sc_params *params, const double *const *nA0, const double *const *nB0,
+                          void *workspace, size_t ws_bytes, void *stream, sc_batch **out) {
+  if (!out) return fail(SC_EINVAL, "out is NULL");
+  *out = nullptr;
+  sc_status st = batch_validate(n, params);
+  if (st != SC_OK) return st;
+  if (!nA0 || !nB0 || !workspace) return fail(SC_EINVAL, "initial fields and workspace must be non-NULL");
+  if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return fail(SC_EINVAL, "workspace must be 256-byte aligned");
+  const size_t need = sc_batch_workspace_bytes(n, params);
+  if (ws_bytes < need) return fail(SC_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, need);
+  sc_batch *b = new (std::nothrow) sc_batch;
+  if (!b) return fail(SC_ENOMEM, "host allocation failed");
+  memset(b, 0, sizeof(*b));
+  b->n = n;
+  b->stream = static_cast<cudaStream_t>(stream);
+  b->ctx = new (std::nothrow) sc_ctx *[n];
+  if (!b->ctx) {
+    delete b;
+    return fail(SC_ENOMEM, "host allocation failed");
+  }
+  for (int k = 0; k < n; ++k) b->ctx[k] = nullptr;
+  char *ws = static_cast<char *>(workspace);
+  size_t off = 0;
+  for (int k = 0; k < n; ++k) {
+    sc_params pk = params[k];
+    pk.variant = 1;  // the batched kernel is the generic one
+    const size_t bytes = layout_of(&pk).total;
+    st = sc_create(&pk, nA0[k], nB0[k], ws + off, bytes, stream, &b->ctx[k]);
+    if (st != SC_OK) {
+      sc_batch_destroy(b);
+      return st;
+    }
+    b->ctx[k]->in_batch = 1;
+    off += bytes;
+  }
+  // tables: per-lattice arguments (parity 0) and the block work list
+  int nitems = 0;
+  batch_table_bytes(n, params, &nitems);
+  b->nitems = nitems;
+  b->tile_y = b->ctx[0]->tile_y;
+  b->args_dev = ws + off;
+  off += align_up(sizeof(StepArgs<double>) * (size_t)n);
+  b->items_dev = reinterpret_cast<int4 *>(ws + off);
+  const int storage = params[0].storage;
+  const size_t arg_size = storage == SC_STORE_F64 ? sizeof(StepArgs<double>) : sizeof(StepArgs<float>);
+  std::string host_args(arg_size * n, '\0');
+  int4 *items = new (std::nothrow) int4[nitems];
+  if (!items) {
+    sc_batch_destroy(b);
+    return fail(SC_ENOMEM, "host allocation failed");
+  }
+  int m = 0;
+  for (int k = 0; k < n; ++k) {
+    sc_ctx *c = b->ctx[k];
+    if (storage == SC_STORE_F64) {
+      StepArgs<double> a = step_args<double>(c);
+      memcpy(&host_args[arg_size * k], &a, arg_size);
+    } else {
+      StepArgs<float> a = step_args<float>(c);
+      memcpy(&host_args[arg_size * k], &a, arg_size);
+    }
+    const int gx = (c->p.nx + 31) / 32, gy = (c->p.ny + c->tile_y - 1) / c->tile_y,
+              gz = (c->p.nz + c->tile_z - 1) / c->tile_z;
+    for (int z = 0; z < gz; ++z)
+      for (int y = 0; y < gy; ++y)
+        for (int x = 0; x < gx; ++x)
+          if (m < nitems) items[m++] = make_int4(k, x, y, z);
+  }
+  if (m != nitems) {
+    delete[] items;
+    sc_batch_destroy(b);
+    return fail(SC_EINVAL, "batch work list size mismatch (%d vs %d)", m, nitems);
+  }
+  cudaError_t e = cudaMemcpyAsync(b->args_dev, host_args.data(), arg_size * n, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->items_dev, items, sizeof(int4) * nitems, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  delete[] items;
+  if (e != cudaSuccess) {
+    sc_batch_destroy(b);
+    return fail(SC_ECUDA, "uploading batch tables: %s", cudaGetErrorString(e));
+  }
+  const int lat = params[0].lattice == SC_D3Q19 ? kD3Q19 : kD2Q9;
+  const int sten = params[0].stencil == SC_FORCE_E6 ? kE6 : kE4;
+  switch (storage) {
+    case SC_STORE_F32: b->kernel = batched_kernel_f32(lat, sten, b->tile_y, &b->smem); break;
+    case SC_STORE_F16: b->kernel = batched_kernel_f16(lat, sten, b->tile_y, &b->smem); break;
+    case SC_STORE_BF16: b->kernel = batched_kernel_bf16(lat, sten, b->tile_y, &b->smem); break;
+    default: b->kernel = batched_kernel_f64(lat, sten, b->tile_y, &b->smem); break;
+  }
+  if (!b->kernel) {
+    sc_batch_destroy(b);
+    return fail(SC_EUNSUPPORTED, "no batched kernel for this lattice / stencil / tile_y");
+  }
+  // a graph of kGraphSteps chained launches, swap = 0, 1, 0, 1, ...
+  e = cudaGraphCreate(&b->graph, 0);
+  cudaGraphNode_t prev = nullptr;
+  int swaps[2] = {0, 1};
+  void *argp = b->args_dev;
+  void *itemp = b->items_dev;
+  for (int t = 0; t < kGraphSteps && e == cudaSuccess; ++t) {
+    void *kp[3] = {&argp, &itemp, &swaps[t & 1]};
+    cudaKernelNodeParams np;
+    memset(&np, 0, sizeof(np));
+    np.func = const_cast<void *>(b->kernel);
+    np.gridDim = dim3(nitems);
+    np.blockDim = dim3(32, b->tile_y);
+    np.sharedMemBytes = (unsigned)b->smem;
+    np.kernelParams = kp;
+    cudaGraphNode_t node;
+    e = cudaGraphAddKernelNode(&node, b->graph, prev ? &prev : nullptr, prev ? 1 : 0, &np);
+    prev = node;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (e != cudaSuccess) {
+    sc_batch_destroy(b);
+    return fail(SC_ECUDA, "building the batch graph: %s", cudaGetErrorString(e));
+  }
+  *out = b;
+  return SC_OK;
+}
+
+sc_status sc_batch_step(sc_batch *b, int64_t nsteps) {
+  if (!b) return fail(SC_EINVAL, "batch is NULL");
+  if (nsteps < 0) return fail(SC_EINVAL, "nsteps must be >= 0");
+  auto single = [&]() -> cudaError_t {
+    void *argp = b->args_dev;
+    void *itemp = b->items_dev;
+    int swap = (int)(b->steps & 1);
+    void *kp[3] = {&argp, &itemp, &swap};
+    cudaError_t e = cudaLaunchKernel(b->kernel, dim3(b->nitems), dim3(32, b->tile_y), kp, b->smem, b->stream);
+    b->steps++;
+    b->launches++;
+    return e;
+  };
+  while (nsteps > 0) {
+    cudaError_t e;
+    if ((b->steps & 1) == 0 && nsteps >= kGraphSteps) {
+      e = cudaGraphLaunch(b->exec, b->stream);
+      b->steps += kGraphSteps;
+      b->launches += kGraphSteps;
+      nsteps -= kGraphSteps;
+    } else {
+      e = single();
+      nsteps -= 1;
+    }
+    if (e != cudaSuccess) return fail(SC_ECUDA, "batched step: %s", cudaGetErrorString(e));
+  }
+  for (int k = 0; k < b->n; ++k) {
+    b->ctx[k]->cur = (int)(b->steps & 1);
+    b->ctx[k]->steps = b->steps;
+    b->ctx[k]->launches = b->launches;
+  }
+  return SC_OK;
+}
+
+sc_ctx *sc_batch_member(sc_batch *b, int32_t k) {
+  if (!b || k < 0 || k >= b->n) {
+    fail(SC_EINVAL, "no such batch member");
+    return nullptr;
+  }
+  return b->ctx[k];
+}
+
+int64_t sc_batch_launches(const sc_batch *b) { return b ? b->launches : 0; }
+
+void sc_batch_destroy(sc_batch *b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->ctx)
+    for (int k = 0; k < b->n; ++k) delete b->ctx[k];
+  delete[] b->ctx;
+  delete b;
 }
 
 int64_t sc_kernel_launches(const sc_ctx *c) { return c ? c->launches : 0; }

@@ -23,4 +23,13 @@ cudaError_t launch_step_f16(const StepLaunch &l, const StepArgs<float> &a);
 cudaError_t launch_step_bf16(const StepLaunch &l, const StepArgs<float> &a);
 cudaError_t launch_step_f64(const StepLaunch &l, const StepArgs<double> &a);
 
+// The batched step kernel for one (lattice, stencil, tile_y) combination, as a
+// function pointer for graph kernel nodes (nullptr if unsupported); *smem
+// receives its dynamic shared-memory bytes.  Parameters: (const StepArgs *args,
+// const int4 *items, int swap), block (32, tile_y), one block per item.
+const void *batched_kernel_f32(int lattice, int stencil, int tile_y, size_t *smem);
+const void *batched_kernel_f16(int lattice, int stencil, int tile_y, size_t *smem);
+const void *batched_kernel_bf16(int lattice, int stencil, int tile_y, size_t *smem);
+const void *batched_kernel_f64(int lattice, int stencil, int tile_y, size_t *smem);
+
 }  // namespace scgb

@@ -3,3 +3,6 @@
 cudaError_t scgb::launch_step_bf16(const StepLaunch &l, const StepArgs<float> &a) {
   return launch_any<__nv_bfloat16, float>(l, a);
 }
+const void *scgb::batched_kernel_bf16(int lattice, int stencil, int tile_y, size_t *smem) {
+  return batched_any<__nv_bfloat16, float>(lattice, stencil, tile_y, smem);
+}

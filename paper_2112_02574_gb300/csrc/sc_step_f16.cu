@@ -1,3 +1,6 @@
 // Step-kernel instantiations: FP16 scaled deviation storage, FP32 collision.
 #include "sc_step_inst.cuh"
 cudaError_t scgb::launch_step_f16(const StepLaunch &l, const StepArgs<float> &a) { return launch_any<__half, float>(l, a); }
+const void *scgb::batched_kernel_f16(int lattice, int stencil, int tile_y, size_t *smem) {
+  return batched_any<__half, float>(lattice, stencil, tile_y, smem);
+}

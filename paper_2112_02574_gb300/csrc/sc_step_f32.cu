@@ -1,3 +1,6 @@
 // Step-kernel instantiations: FP32 deviation storage, FP32 collision.
 #include "sc_step_inst.cuh"
 cudaError_t scgb::launch_step_f32(const StepLaunch &l, const StepArgs<float> &a) { return launch_any<float, float>(l, a); }
+const void *scgb::batched_kernel_f32(int lattice, int stencil, int tile_y, size_t *smem) {
+  return batched_any<float, float>(lattice, stencil, tile_y, smem);
+}

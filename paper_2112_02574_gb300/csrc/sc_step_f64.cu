@@ -2,3 +2,6 @@
 // instantiation the parity tests compare with the FP64 oracle most tightly).
 #include "sc_step_inst.cuh"
 cudaError_t scgb::launch_step_f64(const StepLaunch &l, const StepArgs<double> &a) { return launch_any<double, double>(l, a); }
+const void *scgb::batched_kernel_f64(int lattice, int stencil, int tile_y, size_t *smem) {
+  return batched_any<double, double>(lattice, stencil, tile_y, smem);
+}

@@ -68,4 +68,32 @@ cudaError_t launch_any(const StepLaunch &l, const StepArgs<CT> &a) {
   return cudaErrorInvalidValue;
 }
 
+template <int LAT, int STEN, class ST, class CT, int TY>
+const void *batched_one(size_t *smem) {
+  constexpr size_t bytes = step_smem_bytes<LAT, STEN, CT, TY>();
+  auto *k = sc_step_batched<LAT, STEN, ST, CT, TY>;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)) != cudaSuccess) return nullptr;
+  *smem = bytes;
+  return reinterpret_cast<const void *>(k);
+}
+
+template <int LAT, int STEN, class ST, class CT>
+const void *batched_ty(int ty, size_t *smem) {
+  switch (ty) {
+    case 1: return batched_one<LAT, STEN, ST, CT, 1>(smem);
+    case 2: return batched_one<LAT, STEN, ST, CT, 2>(smem);
+    case 4: return batched_one<LAT, STEN, ST, CT, 4>(smem);
+    case 8: return batched_one<LAT, STEN, ST, CT, 8>(smem);
+    default: return nullptr;
+  }
+}
+
+template <class ST, class CT>
+const void *batched_any(int lat, int sten, int ty, size_t *smem) {
+  if (lat == kD3Q19 && sten == kE4) return batched_ty<kD3Q19, kE4, ST, CT>(ty, smem);
+  if (lat == kD3Q19 && sten == kE6) return batched_ty<kD3Q19, kE6, ST, CT>(ty, smem);
+  if (lat == kD2Q9 && sten == kE4) return batched_ty<kD2Q9, kE4, ST, CT>(ty, smem);
+  return nullptr;
+}
+
 }  // namespace scgb

@@ -217,8 +217,9 @@ __device__ __forceinline__ void collide_site(const StepArgs<CT> &a, const P2<CT>
   }
 }
 
+// One block's work: the column (bx, by) x z-chunk bz of the lattice described by a.
 template <int LAT, int STEN, class ST, class CT, int TY>
-__global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 16 / TY)) sc_step_kernel(const StepArgs<CT> a) {
+__device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by, int bz, unsigned char *smem_raw) {
   using L = Lattice<LAT>;
   using SN = Stencil<LAT, STEN>;
   constexpr int Q = L::Q;
@@ -231,14 +232,13 @@ __global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 16 / TY)) sc_step_ker
   constexpr int NT = 32 * TY;
   constexpr bool KEEP = (HZ <= 1);  // own populations stay in registers until collided
 
-  extern __shared__ __align__(128) unsigned char smem_raw[];
   P2<CT> *s_dn = reinterpret_cast<P2<CT> *>(smem_raw);  // [NPL][PLANE]
   P2<CT> *s_psi = s_dn + NPL * PLANE;                   // [NPL][PLANE]
 
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const int64_t N = a.N;
-  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * TY, z0 = blockIdx.z * a.tile_z;
+  const int x0 = bx * 32, y0 = by * TY, z0 = bz * a.tile_z;
   const int zend = min(z0 + a.tile_z, nz);
   const ST *__restrict__ src = static_cast<const ST *>(a.src);
   ST *__restrict__ dst = static_cast<ST *>(a.dst);
@@ -298,6 +298,29 @@ __global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 16 / TY)) sc_step_ker
     }
     slot = (slot + 1 == NPL) ? 0 : slot + 1;
   }
+}
+
+template <int LAT, int STEN, class ST, class CT, int TY>
+__global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 16 / TY)) sc_step_kernel(const StepArgs<CT> a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  step_block<LAT, STEN, ST, CT, TY>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+}
+
+// Batched form: one launch steps several lattices.  Block b works on item
+// items[b] = (lattice, bx, by, bz); lattice l's arguments are args[l] (read
+// from global memory), with source and destination swapped when swap != 0.
+template <int LAT, int STEN, class ST, class CT, int TY>
+__global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 16 / TY))
+    sc_step_batched(const StepArgs<CT> *__restrict__ args, const int4 *__restrict__ items, int swap) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int4 it = items[blockIdx.x];
+  StepArgs<CT> a = args[it.x];
+  if (swap) {
+    const void *t = a.src;
+    a.src = a.dst;
+    a.dst = const_cast<void *>(t);
+  }
+  step_block<LAT, STEN, ST, CT, TY>(a, it.y, it.z, it.w, smem_raw);
 }
 
 }  // namespace scgb

@@ -1,0 +1,76 @@
+"""The batched radius sweep: lattices of uneven sizes and parameters stepped
+together by one launch per time step (replayed from a CUDA graph).  Each
+member must match the same lattice stepped on its own, bit for bit (same
+kernel body and arithmetic), and the FP64 member must match the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import sc_synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2112_02574_gb300 import binding
+
+    return binding
+
+
+def droplet_set(B, storage):
+    """Four odd-sized cubes (side 2 floor(2R) + 1), alternately symmetric and asymmetric."""
+    out = []
+    for k, R in enumerate((4.0, 5.5, 7.0, 8.5)):
+        L = 2 * int(2 * R) + 1
+        shape = (L, L, L)
+        sym = k % 2 == 0
+        kw = dict(G=2.5, G_self=(0.0, 0.0) if sym else (-0.4, 0.0), tau=(1.0, 1.0))
+        p = B.make_params(shape, lattice=B.SC_D3Q19, psi_self=B.SC_PSI_EXP, storage=storage, tile_z=7, **kw)
+        f = S.droplet(shape[::-1], (L // 2,) * 3, R, n_in=0.85, n_out=0.15, amplitude=1e-3, seed=100 + k)
+        out.append((p, f, kw, shape))
+    return out
+
+
+@pytest.mark.parametrize("nsteps", [9, 70])
+def test_batch_members_equal_single_runs(B, nsteps):
+    sets = droplet_set(B, B.SC_STORE_F32)
+    batch = B.Batch([s[0] for s in sets], [s[1] for s in sets])
+    batch.step(nsteps)
+    assert batch.launches == nsteps
+    for (p, f, kw, shape), m in zip(sets, batch.members):
+        single = B.Simulation(B.make_params(shape, lattice=B.SC_D3Q19, psi_self=B.SC_PSI_EXP,
+                                            storage=B.SC_STORE_F32, tile_z=7, variant=1, **kw), *f)
+        single.step(nsteps)
+        np.testing.assert_array_equal(m.populations().cpu().numpy(), single.populations().cpu().numpy())
+
+
+def test_batch_fp64_member_matches_oracle(B):
+    sets = droplet_set(B, B.SC_STORE_F64)
+    batch = B.Batch([s[0] for s in sets], [s[1] for s in sets])
+    batch.step(12)
+    p, f, kw, shape = sets[1]
+    op = oracle.Params(shape=shape, lattice=oracle.D3Q19, psi_self=oracle.PSI_EXP, **kw)
+    ref = oracle.step(op, oracle.init(op, *f), 12)
+    got = batch.members[1].populations().cpu().numpy()
+    assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+def test_batch_member_analysis_and_guard(B):
+    sets = droplet_set(B, B.SC_STORE_F32)
+    batch = B.Batch([s[0] for s in sets], [s[1] for s in sets])
+    batch.step(33)
+    m = batch.members[3]
+    L = m.shape[0]
+    rows, out = B.surface_of_tension(m, (L // 2,) * 3, 0.5)
+    assert np.isfinite(out.cpu().numpy()[:4]).all()
+    with pytest.raises(B.ScError) as e:
+        m.step(1)
+    assert e.value.status == B.SC_EINVAL
