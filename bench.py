@@ -30,7 +30,9 @@ SHAPE = (128, 128, 128)
 RADIUS = 24.0
 G_CROSS = 3.6  # G c_s^2 = 1.2: the largest tested coupling that is stable in three dimensions at tau = 1
 INNER = 2048  # time steps per benchmark step (section 4: delta t = 2^11); --inner overrides for profiling
-BYTES_PER_SITE = {"f32": 304, "f16": 152, "bf16": 152, "f64": 608}  # 2 comps x 19 pops x (read + write) x bytes
+# 2 comps x 19 pops x (read + write) x bytes, plus for 16-bit storage the FP32 reference-density pair of
+# each site (read + write, 16 B)
+BYTES_PER_SITE = {"f32": 304, "f16": 168, "bf16": 168, "f64": 608}
 # DRAM bytes (read + write) of one step launch on this workload, from an ncu capture
 # (profiles/sc_step_staged_d3q19_128cube.md); reported only while the kernel sources
 # still hash to the captured version.
@@ -237,7 +239,7 @@ def run_gpu(args, rank, world, local_rank):
     st = {"f32": B.SC_STORE_F32, "f16": B.SC_STORE_F16, "bf16": B.SC_STORE_BF16, "f64": B.SC_STORE_F64}[storage]
     params = B.make_params(SHAPE, lattice=B.SC_D3Q19, stencil=B.SC_FORCE_E4, psi_self=B.SC_PSI_EXP, storage=st,
                            tau=(1.0, 1.0), G=G_CROSS, G_self=(0.0, 0.0), tile_y=args.tile_y, tile_z=args.tile_z,
-                           variant=args.variant)
+                           variant=args.variant, stages=args.stages, blocks_per_sm=args.blocks_per_sm)
     nA0, nB0 = fields()
     stream = torch.cuda.Stream(dev)
     sites = SHAPE[0] * SHAPE[1] * SHAPE[2]
@@ -333,7 +335,7 @@ def run_gpu(args, rank, world, local_rank):
 
     batch = None
     if not args.no_batch and rank == 0:
-        batch = batch_block(B, dev, stream)
+        batch = batch_block(B, dev, stream, value / world if storage == "f32" else None)
 
     if rank != 0:
         return
@@ -357,14 +359,17 @@ def run_gpu(args, rank, world, local_rank):
 
 
 def sweep_droplets():
-    """The batched radius sweep: 16 droplets, R_k = 8 + 32 k / 15, cubes of odd side 2 floor(2R) + 1
-    (about 4R, centre on a node), even k symmetric, odd k asymmetric (G_AA c_s^2 = -0.2)."""
+    """The batched radius sweep: 16 droplets, R_k = 8 + 32 k / 15, cubes of side 4 ceil(R_k) (about 4R,
+    a multiple of 4 so that every member takes the staged kernel; centre on a node), even k symmetric,
+    odd k asymmetric (G_AA c_s^2 = -0.2)."""
+    import math
+
     import sc_synth
 
     out = []
     for k in range(16):
         R = 8.0 + 32.0 * k / 15.0
-        L = 2 * int(2 * R) + 1
+        L = 4 * math.ceil(R)
         G_self = (0.0, 0.0) if k % 2 == 0 else (-0.6, 0.0)
         f = sc_synth.droplet((L, L, L), (L // 2,) * 3, R, n_in=0.95, n_out=0.05, amplitude=1e-3,
                              seed=20211206 + 3 + k)
@@ -372,9 +377,12 @@ def sweep_droplets():
     return out
 
 
-def batch_block(B, dev, stream, steps=128):
-    """Throughput of the batched radius sweep (one launch per step, CUDA graph), FP32 and FP16 storage;
-    tile rows chosen by the autotuner."""
+BATCH_CANDIDATES = [(8, 32, 1, 2), (8, 16, 1, 2), (4, 32, 1, 3), (4, 16, 2, 3), (4, 32, 2, 2)]
+
+
+def batch_block(B, dev, stream, plain_mlups, steps=128):
+    """Throughput of the batched radius sweep (one launch per step, CUDA graph) in FP32, FP16 and BF16
+    storage; (tile_y, tile_z, stages, blocks_per_sm) chosen by the autotuner on the whole batch."""
     import torch
 
     from paper_2112_02574_gb300 import tune
@@ -382,13 +390,12 @@ def batch_block(B, dev, stream, steps=128):
     drops = sweep_droplets()
     sites = sum(L ** 3 for L, _, _, _ in drops)
     res = {"lattices": len(drops), "sites": sites, "sides": [L for L, _, _, _ in drops]}
-    for name, code in (("f32", B.SC_STORE_F32), ("f16", B.SC_STORE_F16)):
+    fields_ = [f for _, _, _, f in drops]
+    for name, code in (("f32", B.SC_STORE_F32), ("f16", B.SC_STORE_F16), ("bf16", B.SC_STORE_BF16)):
         plist = [B.make_params((L, L, L), lattice=B.SC_D3Q19, psi_self=B.SC_PSI_EXP, storage=code, G=G_CROSS,
-                               G_self=gs, tile_z=16) for L, _, gs, _ in drops]
-        fields_ = [f for _, _, _, f in drops]
-        ty, _, table = tune.tune_batch_tile_y(plist, fields_, steps=16, device=dev)
-        plist = [B.make_params((L, L, L), lattice=B.SC_D3Q19, psi_self=B.SC_PSI_EXP, storage=code, G=G_CROSS,
-                               G_self=gs, tile_z=16, tile_y=ty) for L, _, gs, _ in drops]
+                               G_self=gs) for L, _, gs, _ in drops]
+        cfg, _, table = tune.tune_batch(plist, fields_, BATCH_CANDIDATES, steps=16, device=dev)
+        plist = [tune.with_config(p, cfg) for p in plist]
         with torch.cuda.stream(stream):
             batch = B.Batch(plist, fields_, device=dev, stream=stream)
             batch.step(64)
@@ -398,8 +405,11 @@ def batch_block(B, dev, stream, steps=128):
             b.record(stream)
             b.synchronize()
         ms = a.elapsed_time(b)
-        res[name] = {"MLUPS": sites * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps, "tile_y": ty,
-                     "tuning": [[t, round(m, 4)] for t, m in table]}
+        mlups = sites * steps / (ms * 1e-3) / 1e6
+        res[name] = {"MLUPS": mlups, "ms_per_step": ms / steps, "staged": batch.staged,
+                     "config": dict(zip(("tile_y", "tile_z", "stages", "blocks_per_sm"), cfg)),
+                     "vs_plain_f32": mlups / plain_mlups if plain_mlups else None,
+                     "tuning": [[list(c), round(m, 4)] for c, m in table]}
         del batch
     return res
 
@@ -437,7 +447,9 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "f64"])
     ap.add_argument("--tile-y", type=int, default=0)
     ap.add_argument("--tile-z", type=int, default=0)
-    ap.add_argument("--variant", type=int, default=0, help="step kernel: 0 auto, 1 generic, 2 TMA-staged")
+    ap.add_argument("--variant", type=int, default=0, help="step kernel: 0 auto, 1 generic, 2 cp.async-staged")
+    ap.add_argument("--stages", type=int, default=0, help="staged kernel pipeline stages (0 default, 1, 2)")
+    ap.add_argument("--blocks-per-sm", type=int, default=0, help="staged kernel register budget (0 default)")
     ap.add_argument("--kernel-events", action="store_true", help="record per-step kernel events in the timed loop")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -59,12 +59,15 @@ typedef enum { SC_D2Q9 = 0, SC_D3Q19 = 1 } sc_lattice;
 typedef enum { SC_FORCE_E4 = 0, SC_FORCE_E6 = 1 } sc_stencil;
 /* Pseudopotential of the self-coupling term: psi = n, or psi = exp(-1/n) (section 4). */
 typedef enum { SC_PSI_N = 0, SC_PSI_EXP = 1 } sc_psi;
-/* Population storage.  Stored values are deviations g_i = f_i - w_i nbar_J from
- * a rest equilibrium with the mean initial density nbar_J; F16/BF16 store
- * g_i * 2^k(J,i) with a power-of-two scale fixed at sc_create.  Collision
- * arithmetic is FP32 for F32/F16/BF16 and FP64 for F64.  In device memory the
- * two components of a direction and site are adjacent ([i][site][J]); this raw
- * layout is what sc_get_state / sc_set_state copy. */
+/* Population storage.  F32/F64 store deviations g_i = f_i - w_i nbar_J from a
+ * rest equilibrium with the mean initial density nbar_J.  F16/BF16 store the
+ * deviation from each site's own rest equilibrium, (f*_i(s) - w_i n_J(s)) 2^k(J)
+ * (F16: a power-of-two scale per component fixed at sc_create; BF16: unscaled), with n_J(s) -- the sum
+ * of the values stored at s, i.e. the site's density when it was written --
+ * kept beside them as an FP32 pair per site.  Collision arithmetic is FP32 for
+ * F32/F16/BF16 and FP64 for F64.  In device memory the two components of a
+ * direction and site are adjacent ([i][site][J]); sc_get_state / sc_set_state
+ * copy that buffer followed, for F16/BF16, by the [site][J] FP32 densities. */
 typedef enum { SC_STORE_F32 = 0, SC_STORE_F16 = 1, SC_STORE_BF16 = 2, SC_STORE_F64 = 3 } sc_storage;
 typedef enum { SC_PROFILE_RADIAL = 0, SC_PROFILE_PLANAR_Z = 1, SC_PROFILE_AXIS_X = 2 } sc_profile_kind;
 
@@ -81,6 +84,10 @@ typedef struct {
   int32_t variant;     /* step kernel: 0 = automatic, 1 = generic (any size, any stencil),
                           2 = cp.async-staged (D3Q19, E4, nx % 32 == 0, nx >= 64,
                           tile_y 4 or 8; tile_y 4 for F64); both compute the same numbers */
+  int32_t stages;      /* staged kernel copy pipeline: 1 or 2 planes in flight; 0 = default */
+  int32_t blocks_per_sm; /* staged kernel register budget: resident blocks per SM it must allow
+                          (tile_y 4: 2 or 3; tile_y 8: 1 or 2); 0 = default.  stages and
+                          blocks_per_sm change speed only, never the numbers */
   double tau[2];       /* tau_A, tau_B > 1/2 (Eq. omega_i) */
   double G;            /* inter-component coupling G */
   double G_self[2];    /* self couplings G_AA, G_BB */
@@ -194,9 +201,12 @@ sc_status sc_run_host(const sc_params *params, const double *nA0, const double *
 /* ---- batches: several lattices stepped by one kernel launch per step ----
  * The batched radius sweep: lattices of different sizes and parameters (same
  * lattice type, stencil, storage and tile_y) stepped together; every time step
- * is ONE launch of the generic step kernel over a work list of (lattice, tile)
- * items, replayed from a CUDA graph of 32 chained launches (built explicitly,
- * no stream capture).  Each member is an ordinary context for the analysis
+ * is ONE launch of a step kernel over a work list of (lattice, tile) items,
+ * replayed from a CUDA graph of 32 chained launches (built explicitly, no
+ * stream capture).  The kernel is the staged one when every member can take it
+ * (variant 0 or 2, D3Q19, E4, nx >= 32 a multiple of the chunk sites; members
+ * then share stages and blocks_per_sm), else the generic one; a member with
+ * variant 2 in a batch that cannot be staged is an error (SC_EINVAL).  Each member is an ordinary context for the analysis
  * entry points (sc_moments, sc_pressure_profile, sc_bulk_pressure_at, ...);
  * sc_step refuses batch members. */
 typedef struct sc_batch sc_batch;
@@ -212,6 +222,8 @@ sc_status sc_batch_step(sc_batch *batch, int64_t nsteps);
 sc_ctx *sc_batch_member(sc_batch *batch, int32_t k);
 /* Batched step launches issued so far (each steps every member once). */
 int64_t sc_batch_launches(const sc_batch *batch);
+/* Step kernel of the batch: 1 generic, 2 staged (0 for NULL). */
+int32_t sc_batch_variant(const sc_batch *batch);
 void sc_batch_destroy(sc_batch *batch);
 
 /* Number of step-kernel launches issued by this context so far. */

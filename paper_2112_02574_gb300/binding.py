@@ -37,18 +37,20 @@ class sc_params(ctypes.Structure):
         ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
         ("lattice", ctypes.c_int32), ("stencil", ctypes.c_int32), ("psi_self", ctypes.c_int32),
         ("storage", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("tile_z", ctypes.c_int32),
-        ("variant", ctypes.c_int32),
+        ("variant", ctypes.c_int32), ("stages", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
         ("tau", ctypes.c_double * 2), ("G", ctypes.c_double), ("G_self", ctypes.c_double * 2),
     ]
 
 
 def make_params(shape, lattice=SC_D3Q19, stencil=SC_FORCE_E4, psi_self=SC_PSI_EXP, storage=SC_STORE_F32,
-                tau=(1.0, 1.0), G=0.0, G_self=(0.0, 0.0), tile_y=0, tile_z=0, variant=0) -> sc_params:
-    """sc_params for a lattice of shape (nx, ny, nz); variant 0 auto, 1 generic, 2 staged step kernel."""
+                tau=(1.0, 1.0), G=0.0, G_self=(0.0, 0.0), tile_y=0, tile_z=0, variant=0, stages=0,
+                blocks_per_sm=0) -> sc_params:
+    """sc_params for a lattice of shape (nx, ny, nz); variant 0 auto, 1 generic, 2 staged step
+    kernel; stages / blocks_per_sm tune the staged kernel (0 = library default)."""
     nx, ny, nz = shape
     return sc_params(int(nx), int(ny), int(nz), int(lattice), int(stencil), int(psi_self), int(storage),
-                     int(tile_y), int(tile_z), int(variant), (ctypes.c_double * 2)(*tau), float(G),
-                     (ctypes.c_double * 2)(*G_self))
+                     int(tile_y), int(tile_z), int(variant), int(stages), int(blocks_per_sm),
+                     (ctypes.c_double * 2)(*tau), float(G), (ctypes.c_double * 2)(*G_self))
 
 
 def _load():
@@ -80,6 +82,7 @@ def _load():
         "sc_batch_step": (I32, [V, I64]),
         "sc_batch_member": (V, [V, I32]),
         "sc_batch_launches": (I64, [V]),
+        "sc_batch_variant": (I32, [V]),
         "sc_batch_destroy": (None, [V]),
         "sc_reference_density": (I32, [V, ctypes.POINTER(D)]),
         "sc_destroy": (None, [V]),
@@ -227,6 +230,10 @@ def sc_batch_member(batch, k: int):
 
 def sc_batch_launches(batch) -> int:
     return lib.sc_batch_launches(batch)
+
+
+def sc_batch_variant(batch) -> int:
+    return lib.sc_batch_variant(batch)
 
 
 def sc_batch_destroy(batch):
@@ -380,6 +387,11 @@ class Batch:
     @property
     def launches(self) -> int:
         return sc_batch_launches(self.handle)
+
+    @property
+    def staged(self) -> bool:
+        """True when the batch steps with the staged kernel."""
+        return sc_batch_variant(self.handle) == 2
 
 
 def surface_of_tension(sim: Simulation, centre, bin_width=0.5, nbins=None, in_node=None, out_node=None,

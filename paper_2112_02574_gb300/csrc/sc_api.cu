@@ -55,10 +55,36 @@ size_t store_bytes(int storage) {
   }
 }
 
+// Sites per 16-byte copy chunk of a population row (both components).
+int chunk_sites(int storage) { return storage == SC_STORE_F64 ? 1 : (storage == SC_STORE_F32 ? 2 : 4); }
+
 bool staged_eligible(const sc_params *p, int tile_y) {
-  if (p->lattice != SC_D3Q19 || p->stencil != SC_FORCE_E4 || p->nx % 32 != 0 || p->nx < 64) return false;
+  if (p->lattice != SC_D3Q19 || p->stencil != SC_FORCE_E4 || p->nx < 32 || p->nx % chunk_sites(p->storage) != 0)
+    return false;
   if (p->storage == SC_STORE_F64) return tile_y == 4;
   return tile_y == 4 || tile_y == 8;
+}
+
+// Kernel choice and tiles (measured sweeps at 128^3 and 256^3 set the defaults).
+int staged_default_tile_y(const sc_params *p) { return p->storage == SC_STORE_F64 ? 4 : 8; }
+bool use_staged(const sc_params *p) {
+  if (p->variant == 1) return false;
+  return staged_eligible(p, p->tile_y ? p->tile_y : staged_default_tile_y(p));
+}
+int default_tile_y(const sc_params *p) {
+  if (p->tile_y) return p->tile_y;
+  if (use_staged(p)) return staged_default_tile_y(p);
+  return p->lattice == SC_D3Q19 ? 8 : 4;
+}
+int effective_stages(const sc_params *p, int tile_y) { return p->stages ? p->stages : (tile_y == 8 ? 1 : 2); }
+int effective_blocks_per_sm(const sc_params *p, int tile_y) {
+  if (p->blocks_per_sm) return p->blocks_per_sm;
+  return tile_y == 8 ? 2 : (p->storage == SC_STORE_F64 ? 2 : 3);
+}
+int default_tile_z(const sc_params *p) {
+  if (p->lattice == SC_D2Q9) return 1;
+  const int want = p->tile_z ? p->tile_z : 32;
+  return want < p->nz ? want : p->nz;
 }
 
 sc_status validate(const sc_params *p) {
@@ -76,9 +102,16 @@ sc_status validate(const sc_params *p) {
     return fail(SC_EINVAL, "tile_y must be 0, 1, 2, 4 or 8");
   if (p->tile_z < 0) return fail(SC_EINVAL, "tile_z must be >= 0");
   if (p->variant < 0 || p->variant > 2) return fail(SC_EINVAL, "variant must be 0, 1 or 2");
-  if (p->variant == 2 && !staged_eligible(p, p->tile_y ? p->tile_y : 4))
-    return fail(SC_EINVAL, "the staged step kernel needs D3Q19, E4, nx %% 32 == 0, nx >= 64 and tile_y 4 or 8 "
-                           "(4 for F64 storage)");
+  if (p->stages < 0 || p->stages > 2) return fail(SC_EINVAL, "stages must be 0, 1 or 2");
+  if (p->blocks_per_sm < 0 || p->blocks_per_sm > 3) return fail(SC_EINVAL, "blocks_per_sm must be 0 .. 3");
+  if (p->variant == 2 && !staged_eligible(p, p->tile_y ? p->tile_y : staged_default_tile_y(p)))
+    return fail(SC_EINVAL, "the staged step kernel needs D3Q19, E4, nx >= 32, nx a multiple of %d for this "
+                           "storage and tile_y 4 or 8 (4 for F64 storage)", chunk_sites(p->storage));
+  if (use_staged(p) && p->blocks_per_sm) {
+    const int ty = default_tile_y(p), lo = ty == 8 ? 1 : 2, hi = ty == 8 ? 2 : 3;
+    if (p->blocks_per_sm < lo || p->blocks_per_sm > hi)
+      return fail(SC_EINVAL, "blocks_per_sm must be 0 or %d .. %d for the staged kernel with tile_y %d", lo, hi, ty);
+  }
   for (int J = 0; J < 2; ++J)
     if (!(p->tau[J] > 0.5) || !isfinite(p->tau[J])) return fail(SC_EINVAL, "tau[%d] must be > 1/2", J);
   if (!isfinite(p->G) || !isfinite(p->G_self[0]) || !isfinite(p->G_self[1]))
@@ -88,8 +121,11 @@ sc_status validate(const sc_params *p) {
 
 struct Layout {
   size_t pop_bytes;  // one population buffer
-  size_t off_pop[2], off_fields, off_partial, off_status, total;
+  size_t ref_bytes;  // one local-reference density buffer (16-bit storage), else 0
+  size_t off_pop[2], off_ref[2], off_fields, off_partial, off_status, total;
 };
+
+bool is_local_ref(int storage) { return storage == SC_STORE_F16 || storage == SC_STORE_BF16; }
 
 Layout layout_of(const sc_params *p) {
   Layout L;
@@ -100,6 +136,11 @@ Layout layout_of(const sc_params *p) {
   off = align_up(off + L.pop_bytes);
   L.off_pop[1] = off;
   off = align_up(off + L.pop_bytes);
+  L.ref_bytes = is_local_ref(p->storage) ? (size_t)N * 2 * sizeof(float) : 0;
+  L.off_ref[0] = off;
+  off = align_up(off + L.ref_bytes);
+  L.off_ref[1] = off;
+  off = align_up(off + L.ref_bytes);
   L.off_fields = off;
   off = align_up(off + (size_t)4 * N * sizeof(double));
   L.off_partial = off;
@@ -110,21 +151,6 @@ Layout layout_of(const sc_params *p) {
   return L;
 }
 
-// Kernel choice and tiles (a measured sweep at 128^3 set the defaults).
-bool use_staged(const sc_params *p) {
-  if (p->variant == 1) return false;
-  return staged_eligible(p, p->tile_y ? p->tile_y : 4);
-}
-int default_tile_y(const sc_params *p) {
-  if (p->tile_y) return p->tile_y;
-  if (use_staged(p)) return 4;
-  return p->lattice == SC_D3Q19 ? 8 : 4;
-}
-int default_tile_z(const sc_params *p) {
-  if (p->lattice == SC_D2Q9) return 1;
-  const int want = p->tile_z ? p->tile_z : (use_staged(p) ? 16 : 32);
-  return want < p->nz ? want : p->nz;
-}
 
 }  // namespace
 
@@ -141,7 +167,7 @@ struct sc_ctx {
   Layout L;
   int cur;  // buffer holding the current state
   int tile_y, tile_z;
-  int staged;
+  int staged, stages, blocks_per_sm;
   double nbar[2], psibar[2];
   double scale[2][19], inv_scale[2][19];
   int64_t launches;
@@ -158,6 +184,7 @@ struct sc_batch {
   int4 *items_dev;    // (lattice, bx, by, bz) per block
   int nitems;
   int tile_y;
+  int staged;         // members step with the staged kernel
   const void *kernel;
   size_t smem;
   cudaGraph_t graph;
@@ -175,6 +202,7 @@ double *partial_of(sc_ctx *c) { return reinterpret_cast<double *>(c->ws + c->L.o
 PopArgs pop_args(sc_ctx *c, int buf) {
   PopArgs a;
   a.buf = c->ws + c->L.off_pop[buf];
+  a.nref = c->L.ref_bytes ? reinterpret_cast<float2 *>(c->ws + c->L.off_ref[buf]) : nullptr;
   a.nx = c->p.nx;
   a.ny = c->p.ny;
   a.nz = c->p.nz;
@@ -260,14 +288,14 @@ StepArgs<CT> step_args(sc_ctx *c) {
   a.guo = pair<CT>(1.0 - 0.5 / c->p.tau[0], 1.0 - 0.5 / c->p.tau[1]);
   a.gself = pair<CT>(-c->p.G_self[0] * cs2, -c->p.G_self[1] * cs2);
   a.psibar = pair<CT>(c->psibar[0], c->psibar[1]);
-  for (int i = 0; i < 19; ++i) {
-    a.scale[i] = pair<CT>(c->scale[0][i], c->scale[1][i]);
-    a.inv_scale[i] = pair<CT>(c->inv_scale[0][i], c->inv_scale[1][i]);
-  }
+  a.scale = pair<CT>(c->scale[0][0], c->scale[1][0]);
+  a.inv_scale = pair<CT>(c->inv_scale[0][0], c->inv_scale[1][0]);
   a.gcross = CT(-c->p.G * cs2);
   a.self_on = (c->p.G_self[0] != 0.0 || c->p.G_self[1] != 0.0) ? 1 : 0;
   a.psi_exp = c->p.psi_self == SC_PSI_EXP ? 1 : 0;
   a.err = status_word(c);
+  a.nsrc = c->L.ref_bytes ? reinterpret_cast<const float2 *>(c->ws + c->L.off_ref[c->cur]) : nullptr;
+  a.ndst = c->L.ref_bytes ? reinterpret_cast<float2 *>(c->ws + c->L.off_ref[1 - c->cur]) : nullptr;
   return a;
 }
 
@@ -277,6 +305,8 @@ sc_status launch_one_step(sc_ctx *c) {
   l.stencil = c->p.stencil == SC_FORCE_E6 ? kE6 : kE4;
   l.tile_y = c->tile_y;
   l.staged = c->staged;
+  l.stages = c->stages;
+  l.blocks_per_sm = c->blocks_per_sm;
   l.grid = dim3((c->p.nx + 31) / 32, (c->p.ny + c->tile_y - 1) / c->tile_y, (c->p.nz + c->tile_z - 1) / c->tile_z);
   l.stream = c->stream;
   cudaError_t e;
@@ -375,6 +405,8 @@ sc_status sc_create(const sc_params *params, const double *nA0, const double *nB
   c->tile_y = default_tile_y(params);
   c->tile_z = default_tile_z(params);
   c->staged = use_staged(params) ? 1 : 0;
+  c->stages = effective_stages(params, c->tile_y);
+  c->blocks_per_sm = effective_blocks_per_sm(params, c->tile_y);
   c->fields_at = -1;
   double mean[2], maxdev[2];
   cudaError_t e = cudaMemsetAsync(c->ws + L.off_status, 0, kStatusBytes, c->stream);
@@ -390,13 +422,16 @@ sc_status sc_create(const sc_params *params, const double *nA0, const double *nB
   for (int J = 0; J < 2; ++J) {
     c->nbar[J] = mean[J];
     c->psibar[J] = params->psi_self == SC_PSI_EXP ? exp(-1.0 / mean[J]) : mean[J];
+    double s = 1.0;
+    if (params->storage == SC_STORE_F16) {
+      // stored values are deviations from each site's own rest equilibrium, of order
+      // w_i n |u| (plus the non-equilibrium part); take 0.1 w_0 n_max (w_0 the largest
+      // weight) as their scale and the largest power of two keeping it <= 2^10 (FP16 max
+      // 65504: x64 headroom; the smallest weight is 1/12 of w_0, far from underflow)
+      const double m = 0.1 * lattice_w(params->lattice, 0) * fmax(mean[J] + maxdev[J], 1e-3);
+      s = ldexp(1.0, (int)floor(log2(1024.0 / m)));
+    }
     for (int i = 0; i < 19; ++i) {
-      double s = 1.0;
-      if (params->storage == SC_STORE_F16 && i < c->Q) {
-        // largest power of two keeping max |g| * s <= 2^11 (FP16 max 65504: x32 headroom)
-        const double m = lattice_w(params->lattice, i) * fmax(maxdev[J], 1e-3);
-        s = ldexp(1.0, (int)floor(log2(2048.0 / m)));
-      }
       c->scale[J][i] = s;
       c->inv_scale[J][i] = 1.0 / s;
     }
@@ -471,19 +506,27 @@ sc_status sc_set_populations(sc_ctx *c, const double *f) {
   return SC_OK;
 }
 
-size_t sc_state_bytes(const sc_ctx *c) { return c ? c->L.pop_bytes : 0; }
+size_t sc_state_bytes(const sc_ctx *c) { return c ? c->L.pop_bytes + c->L.ref_bytes : 0; }
 
 sc_status sc_get_state(sc_ctx *c, void *dst, size_t bytes) {
   if (!c || !dst) return fail(SC_EINVAL, "ctx and dst must be non-NULL");
-  if (bytes != c->L.pop_bytes) return fail(SC_EINVAL, "state is %zu bytes, got %zu", c->L.pop_bytes, bytes);
-  SC_CUDA(cudaMemcpyAsync(dst, c->ws + c->L.off_pop[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
+  const size_t need = c->L.pop_bytes + c->L.ref_bytes;
+  if (bytes != need) return fail(SC_EINVAL, "state is %zu bytes, got %zu", need, bytes);
+  SC_CUDA(cudaMemcpyAsync(dst, c->ws + c->L.off_pop[c->cur], c->L.pop_bytes, cudaMemcpyDeviceToDevice, c->stream));
+  if (c->L.ref_bytes)
+    SC_CUDA(cudaMemcpyAsync(static_cast<char *>(dst) + c->L.pop_bytes, c->ws + c->L.off_ref[c->cur], c->L.ref_bytes,
+                            cudaMemcpyDeviceToDevice, c->stream));
   return SC_OK;
 }
 
 sc_status sc_set_state(sc_ctx *c, const void *src, size_t bytes) {
   if (!c || !src) return fail(SC_EINVAL, "ctx and src must be non-NULL");
-  if (bytes != c->L.pop_bytes) return fail(SC_EINVAL, "state is %zu bytes, got %zu", c->L.pop_bytes, bytes);
-  SC_CUDA(cudaMemcpyAsync(c->ws + c->L.off_pop[c->cur], src, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  const size_t need = c->L.pop_bytes + c->L.ref_bytes;
+  if (bytes != need) return fail(SC_EINVAL, "state is %zu bytes, got %zu", need, bytes);
+  SC_CUDA(cudaMemcpyAsync(c->ws + c->L.off_pop[c->cur], src, c->L.pop_bytes, cudaMemcpyDeviceToDevice, c->stream));
+  if (c->L.ref_bytes)
+    SC_CUDA(cudaMemcpyAsync(c->ws + c->L.off_ref[c->cur], static_cast<const char *>(src) + c->L.pop_bytes,
+                            c->L.ref_bytes, cudaMemcpyDeviceToDevice, c->stream));
   c->fields_at = -1;
   return SC_OK;
 }
@@ -614,13 +657,26 @@ sc_status sc_run_host(const sc_params *params, const double *nA0, const double *
 namespace {
 constexpr int kGraphSteps = 32;  // steps per graph replay (even: parity preserved)
 
+// A batch steps every member with the staged kernel when all of them can take
+// it (and none asks for the generic one), else every member with the generic kernel.
+bool batch_staged(int32_t n, const sc_params *params) {
+  for (int k = 0; k < n; ++k)
+    if (!use_staged(&params[k])) return false;
+  return true;
+}
+sc_params member_params(const sc_params &p, bool staged) {
+  sc_params q = p;
+  q.variant = staged ? 2 : 1;
+  return q;
+}
+
 size_t batch_table_bytes(int32_t n, const sc_params *params, int *nitems_out) {
+  const bool staged = batch_staged(n, params);
   int nitems = 0;
   for (int k = 0; k < n; ++k) {
-    const sc_params &p = params[k];
-    const int ty = p.tile_y ? p.tile_y : (p.lattice == SC_D3Q19 ? 8 : 4);
-    const int tz = p.lattice == SC_D2Q9 ? 1 : (p.tile_z ? (p.tile_z < p.nz ? p.tile_z : p.nz) : (p.nz < 32 ? p.nz : 32));
-    nitems += ((p.nx + 31) / 32) * ((p.ny + ty - 1) / ty) * ((p.nz + tz - 1) / tz);
+    const sc_params q = member_params(params[k], staged);
+    const int ty = default_tile_y(&q), tz = default_tile_z(&q);
+    nitems += ((q.nx + 31) / 32) * ((q.ny + ty - 1) / ty) * ((q.nz + tz - 1) / tz);
   }
   if (nitems_out) *nitems_out = nitems;
   return align_up(sizeof(StepArgs<double>) * (size_t)n) + align_up(sizeof(int4) * (size_t)nitems);
@@ -632,12 +688,20 @@ sc_status batch_validate(int32_t n, const sc_params *params) {
   for (int k = 0; k < n; ++k) {
     sc_status st = validate(&params[k]);
     if (st != SC_OK) return st;
-    const sc_params &a = params[0], &b = params[k];
-    const int tya = a.tile_y ? a.tile_y : (a.lattice == SC_D3Q19 ? 8 : 4);
-    const int tyb = b.tile_y ? b.tile_y : (b.lattice == SC_D3Q19 ? 8 : 4);
+  }
+  const bool staged = batch_staged(n, params);
+  const sc_params a = member_params(params[0], staged);
+  const int tya = default_tile_y(&a);
+  for (int k = 0; k < n; ++k) {
+    if (!staged && params[k].variant == 2)
+      return fail(SC_EINVAL, "lattice %d asks for the staged kernel, which not every member of the batch can take", k);
+    const sc_params b = member_params(params[k], staged);
+    const int tyb = default_tile_y(&b);
     if (a.lattice != b.lattice || a.stencil != b.stencil || a.storage != b.storage || tya != tyb)
       return fail(SC_EINVAL, "all lattices of a batch share lattice, stencil, storage and tile_y");
-    if (b.variant == 2) return fail(SC_EINVAL, "a batch steps with the generic kernel (variant 0 or 1)");
+    if (staged && (effective_stages(&a, tya) != effective_stages(&b, tyb) ||
+                   effective_blocks_per_sm(&a, tya) != effective_blocks_per_sm(&b, tyb)))
+      return fail(SC_EINVAL, "all lattices of a batch share stages and blocks_per_sm");
   }
   return SC_OK;
 }
@@ -673,9 +737,9 @@ sc_status sc_batch_create(int32_t n, const sc_params *params, const double *cons
   for (int k = 0; k < n; ++k) b->ctx[k] = nullptr;
   char *ws = static_cast<char *>(workspace);
   size_t off = 0;
+  const bool staged = batch_staged(n, params);
   for (int k = 0; k < n; ++k) {
-    sc_params pk = params[k];
-    pk.variant = 1;  // the batched kernel is the generic one
+    sc_params pk = member_params(params[k], staged);
     const size_t bytes = layout_of(&pk).total;
     st = sc_create(&pk, nA0[k], nB0[k], ws + off, bytes, stream, &b->ctx[k]);
     if (st != SC_OK) {
@@ -733,15 +797,26 @@ sc_status sc_batch_create(int32_t n, const sc_params *params, const double *cons
   }
   const int lat = params[0].lattice == SC_D3Q19 ? kD3Q19 : kD2Q9;
   const int sten = params[0].stencil == SC_FORCE_E6 ? kE6 : kE4;
-  switch (storage) {
-    case SC_STORE_F32: b->kernel = batched_kernel_f32(lat, sten, b->tile_y, &b->smem); break;
-    case SC_STORE_F16: b->kernel = batched_kernel_f16(lat, sten, b->tile_y, &b->smem); break;
-    case SC_STORE_BF16: b->kernel = batched_kernel_bf16(lat, sten, b->tile_y, &b->smem); break;
-    default: b->kernel = batched_kernel_f64(lat, sten, b->tile_y, &b->smem); break;
+  b->staged = staged ? 1 : 0;
+  if (staged) {
+    const int ns = b->ctx[0]->stages, mb = b->ctx[0]->blocks_per_sm;
+    switch (storage) {
+      case SC_STORE_F32: b->kernel = batched_staged_kernel_f32(b->tile_y, ns, mb, &b->smem); break;
+      case SC_STORE_F16: b->kernel = batched_staged_kernel_f16(b->tile_y, ns, mb, &b->smem); break;
+      case SC_STORE_BF16: b->kernel = batched_staged_kernel_bf16(b->tile_y, ns, mb, &b->smem); break;
+      default: b->kernel = batched_staged_kernel_f64(b->tile_y, ns, mb, &b->smem); break;
+    }
+  } else {
+    switch (storage) {
+      case SC_STORE_F32: b->kernel = batched_kernel_f32(lat, sten, b->tile_y, &b->smem); break;
+      case SC_STORE_F16: b->kernel = batched_kernel_f16(lat, sten, b->tile_y, &b->smem); break;
+      case SC_STORE_BF16: b->kernel = batched_kernel_bf16(lat, sten, b->tile_y, &b->smem); break;
+      default: b->kernel = batched_kernel_f64(lat, sten, b->tile_y, &b->smem); break;
+    }
   }
   if (!b->kernel) {
     sc_batch_destroy(b);
-    return fail(SC_EUNSUPPORTED, "no batched kernel for this lattice / stencil / tile_y");
+    return fail(SC_EUNSUPPORTED, "no batched kernel for this lattice / stencil / tile_y / stages / blocks_per_sm");
   }
   // a graph of kGraphSteps chained launches, swap = 0, 1, 0, 1, ...
   e = cudaGraphCreate(&b->graph, 0);
@@ -814,6 +889,7 @@ sc_ctx *sc_batch_member(sc_batch *b, int32_t k) {
 }
 
 int64_t sc_batch_launches(const sc_batch *b) { return b ? b->launches : 0; }
+int32_t sc_batch_variant(const sc_batch *b) { return b ? (b->staged ? 2 : 1) : 0; }
 
 void sc_batch_destroy(sc_batch *b) {
   if (!b) return;

@@ -36,13 +36,22 @@ __device__ __forceinline__ void store_dev(ST *p, double v, double scale) {
 }
 
 struct PopArgs {
-  void *buf;         // stored populations [2][Q][N]
+  void *buf;         // stored populations [Q][N][2]
+  float2 *nref;      // local reference densities [N] (16-bit storage; nullptr otherwise)
   int nx, ny, nz;
   int64_t N;
   double nbar[2];
   double scale[2][19];
   double inv_scale[2][19];
 };
+
+// Natural FP64 population of direction i, component J stored at site s.
+template <int LAT, class ST>
+__device__ __forceinline__ double pop_value(const PopArgs &a, const ST *buf, int i, int J, int64_t s) {
+  const double g = load_dev<ST>(buf + ((int64_t)i * a.N + s) * 2 + J, a.inv_scale[J][i]);
+  const double ref = local_ref<ST>() ? double(J == 0 ? a.nref[s].x : a.nref[s].y) : a.nbar[J];
+  return g + Lattice<LAT>::w(i) * ref;
+}
 
 __device__ __forceinline__ void coords(int64_t s, int nx, int ny, int &x, int &y, int &z) {
   x = int(s % nx);
@@ -57,11 +66,13 @@ __device__ __forceinline__ int64_t site_at(int x, int y, int z, int nx, int ny, 
   return (int64_t)x + (int64_t)nx * (y + (int64_t)ny * z);
 }
 
-// mode 0: initial rest equilibrium from densities n0 (FP64 [2][N]):
-//         buf[J][i][y] = encode(w_i (n0_J(y + xi_i) - nbar_J)), so that the
-//         first pull delivers f_i(x) = w_i n0_J(x);
+// mode 0: initial rest equilibrium from densities n0 (FP64 [2][N]): the value
+//         stored at y for direction i is w_i n0_J(y + xi_i), so that the first
+//         pull delivers f_i(x) = w_i n0_J(x);
 // mode 1: natural populations f (FP64 [2][Q][N]) -> storage (inverse pull);
 // mode 2: storage -> natural populations f.
+// Stored values are relative to w_i nbar_J, or with a local reference to
+// w_i nref_J(y) where nref(y) is the sum of the values stored at y.
 template <int LAT, class ST>
 __global__ void pop_kernel(PopArgs a, int mode, const double *n0A, const double *n0B, double *f) {
   using L = Lattice<LAT>;
@@ -70,26 +81,43 @@ __global__ void pop_kernel(PopArgs a, int mode, const double *n0A, const double 
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
     int x, y, z;
     coords(s, a.nx, a.ny, x, y, z);
+    if (mode == 2) {
+#pragma unroll
+      for (int J = 0; J < 2; ++J)
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+          const int64_t bwd = site_at(x - L::c(i, 0), y - L::c(i, 1), z - L::c(i, 2), a.nx, a.ny, a.nz);
+          f[((int64_t)J * L::Q + i) * N + s] = pop_value<LAT, ST>(a, buf, i, J, bwd);
+        }
+      continue;
+    }
+    double ref[2];
 #pragma unroll
     for (int J = 0; J < 2; ++J) {
-#pragma unroll
-      for (int i = 0; i < L::Q; ++i) {
-        const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
-        const double w = L::w(i);
-        const int64_t fwd = site_at(x + cx, y + cy, z + cz, a.nx, a.ny, a.nz);
-        const int64_t bwd = site_at(x - cx, y - cy, z - cz, a.nx, a.ny, a.nz);
-        ST *slot = buf + (int64_t)i * N * 2 + J;
+      if constexpr (local_ref<ST>()) {
+        double sum = 0.0;
         if (mode == 0) {
-          const double n = (J == 0 ? n0A : n0B)[fwd];
-          store_dev<ST>(slot + s * 2, w * (n - a.nbar[J]), a.scale[J][i]);
-        } else if (mode == 1) {
-          const double fv = f[((int64_t)J * L::Q + i) * N + fwd];
-          store_dev<ST>(slot + s * 2, fv - w * a.nbar[J], a.scale[J][i]);
+          sum = (J == 0 ? n0A : n0B)[s];
         } else {
-          f[((int64_t)J * L::Q + i) * N + s] = load_dev<ST>(slot + bwd * 2, a.inv_scale[J][i]) + w * a.nbar[J];
+#pragma unroll
+          for (int i = 0; i < L::Q; ++i)
+            sum += f[((int64_t)J * L::Q + i) * N + site_at(x + L::c(i, 0), y + L::c(i, 1), z + L::c(i, 2), a.nx, a.ny, a.nz)];
         }
+        ref[J] = double(float(sum));  // the reference is kept in FP32
+      } else {
+        ref[J] = a.nbar[J];
       }
     }
+    if constexpr (local_ref<ST>()) a.nref[s] = make_float2(float(ref[0]), float(ref[1]));
+#pragma unroll
+    for (int J = 0; J < 2; ++J)
+#pragma unroll
+      for (int i = 0; i < L::Q; ++i) {
+        const double w = L::w(i);
+        const int64_t fwd = site_at(x + L::c(i, 0), y + L::c(i, 1), z + L::c(i, 2), a.nx, a.ny, a.nz);
+        const double v = mode == 0 ? w * (J == 0 ? n0A : n0B)[fwd] : f[((int64_t)J * L::Q + i) * N + fwd];
+        store_dev<ST>(buf + ((int64_t)i * N + s) * 2 + J, v - w * ref[J], a.scale[J][i]);
+      }
   }
 }
 
@@ -105,13 +133,12 @@ __global__ void fields_kernel(PopArgs a, int psi_exp, double *fields) {
     coords(s, a.nx, a.ny, x, y, z);
 #pragma unroll
     for (int J = 0; J < 2; ++J) {
-      double dn = 0.0;
+      double n = 0.0;
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) {
         const int64_t bwd = site_at(x - L::c(i, 0), y - L::c(i, 1), z - L::c(i, 2), a.nx, a.ny, a.nz);
-        dn += load_dev<ST>(buf + ((int64_t)i * N + bwd) * 2 + J, a.inv_scale[J][i]);
+        n += pop_value<LAT, ST>(a, buf, i, J, bwd);
       }
-      const double n = a.nbar[J] + dn;
       fields[J * N + s] = n;
       fields[(2 + J) * N + s] = psi_exp ? exp(-1.0 / n) : n;
     }
@@ -174,7 +201,7 @@ __global__ void velocity_kernel(PopArgs a, ForceParams fp, const double *fields,
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) {
         const int64_t bwd = site_at(x - L::c(i, 0), y - L::c(i, 1), z - L::c(i, 2), a.nx, a.ny, a.nz);
-        const double g = load_dev<ST>(buf + ((int64_t)i * N + bwd) * 2 + J, a.inv_scale[J][i]);
+        const double g = pop_value<LAT, ST>(a, buf, i, J, bwd);
 #pragma unroll
         for (int m = 0; m < 3; ++m) j[J][m] += L::c(i, m) * g;
       }
@@ -425,7 +452,7 @@ __global__ void __launch_bounds__(256) totals_partial_kernel(PopArgs a, double *
 #pragma unroll
       for (int i = 0; i < L::Q; ++i) {
         // stored at the collision site: sums over all sites need no pull
-        const double f = load_dev<ST>(buf + ((int64_t)i * N + s) * 2 + J, a.inv_scale[J][i]) + L::w(i) * a.nbar[J];
+        const double f = pop_value<LAT, ST>(a, buf, i, J, s);
         acc[J] += f;
 #pragma unroll
         for (int m = 0; m < 3; ++m) acc[2 + m] += L::c(i, m) * f;

@@ -158,9 +158,11 @@ struct Stencil<kD3Q19, kE6> {
 
 // ---------------------------------------------------------------- storage
 // A component pair (A, B) of one direction and site: stored -> compute pair and
-// back.  F16/BF16 carry a per-(J, i) power-of-two scale so that the deviations
-// sit in the normal range.  SMEM selects plain loads (shared memory) instead of
-// read-only-cache loads (global memory).
+// back.  F16 carries a per-component power-of-two scale that puts the
+// deviations high in the normal range (a power of two changes no rounding of a
+// normal FP16 number, only how far the values sit from underflow and overflow);
+// BF16 has the FP32 exponent range and needs none.  SMEM selects plain loads
+// (shared memory) instead of read-only-cache loads (global memory).
 template <class ST, class CT>
 struct Codec2;
 template <>
@@ -195,13 +197,13 @@ struct Codec2<__half, float> {
 template <>
 struct Codec2<__nv_bfloat16, float> {
   template <bool SMEM>
-  __device__ __forceinline__ static float2 load(const __nv_bfloat16 *p, float2 inv_scale) {
+  __device__ __forceinline__ static float2 load(const __nv_bfloat16 *p, float2) {
     const __nv_bfloat162 h =
         SMEM ? *reinterpret_cast<const __nv_bfloat162 *>(p) : __ldg(reinterpret_cast<const __nv_bfloat162 *>(p));
-    return pmul(__bfloat1622float2(h), inv_scale);
+    return __bfloat1622float2(h);
   }
-  __device__ __forceinline__ static void store(__nv_bfloat16 *p, float2 v, float2 scale) {
-    *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(pmul(v, scale));
+  __device__ __forceinline__ static void store(__nv_bfloat16 *p, float2 v, float2) {
+    *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(v);
   }
 };
 
@@ -220,10 +222,22 @@ struct StepArgs {
   P2<CT> psibar;     // psi(nbar_J)
   int self_on;       // any G_JJ != 0
   int psi_exp;       // psi = exp(-1/n) (else psi = n)
-  P2<CT> scale[19];      // storage scale 2^k(J, i) (1 for F32/F64)
-  P2<CT> inv_scale[19];  // 2^-k(J, i)
+  P2<CT> scale;      // storage scale 2^k(J) (F16; unused for the other storages)
+  P2<CT> inv_scale;  // 2^-k(J)
   unsigned int *err;     // device status word (bit 0: density out of range)
+  // Local reference (F16/BF16 storage): the value stored at site s is
+  // (f*_i(s) - w_i n(s)) 2^k with n(s) the site's density when it was written,
+  // kept as an FP32 pair per site: read from nsrc, written to ndst.
+  const float2 *nsrc;
+  float2 *ndst;
 };
+
+// Storage modes whose populations are deviations from each site's own density
+// (16-bit storage); the 32/64-bit modes use the constant mean density nbar.
+template <class ST>
+__host__ __device__ constexpr bool local_ref() {
+  return sizeof(ST) == 2;
+}
 
 __host__ __device__ __forceinline__ int wrapi(int a, int n) {
   // a in [-n, 2n)

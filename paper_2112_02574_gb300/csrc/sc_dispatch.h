@@ -11,7 +11,9 @@ struct StepLaunch {
   int lattice;  // kD2Q9 / kD3Q19
   int stencil;  // kE4 / kE6
   int tile_y;   // 1, 2, 4 or 8
-  int staged;   // 1: TMA-staged persistent kernel (D3Q19, E4, nx % 32 == 0, nx >= 64)
+  int staged;   // 1: cp.async-staged kernel (D3Q19, E4, nx >= 32, nx a multiple of the chunk sites)
+  int stages;   // staged kernel: pipeline stages, 1 or 2
+  int blocks_per_sm;  // staged kernel: resident blocks per SM its registers allow (tile_y 4: 2 or 3; 8: 1 or 2)
   dim3 grid;    // generic kernel grid
   cudaStream_t stream;
 };
@@ -31,5 +33,12 @@ const void *batched_kernel_f32(int lattice, int stencil, int tile_y, size_t *sme
 const void *batched_kernel_f16(int lattice, int stencil, int tile_y, size_t *smem);
 const void *batched_kernel_bf16(int lattice, int stencil, int tile_y, size_t *smem);
 const void *batched_kernel_f64(int lattice, int stencil, int tile_y, size_t *smem);
+
+// The batched staged step kernel (D3Q19, E4) for (tile_y, stages, blocks_per_sm),
+// same parameters and block shape as above; nullptr if not instantiated.
+const void *batched_staged_kernel_f32(int tile_y, int stages, int blocks_per_sm, size_t *smem);
+const void *batched_staged_kernel_f16(int tile_y, int stages, int blocks_per_sm, size_t *smem);
+const void *batched_staged_kernel_bf16(int tile_y, int stages, int blocks_per_sm, size_t *smem);
+const void *batched_staged_kernel_f64(int tile_y, int stages, int blocks_per_sm, size_t *smem);
 
 }  // namespace scgb

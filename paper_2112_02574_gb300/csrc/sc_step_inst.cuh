@@ -23,27 +23,41 @@ cudaError_t launch_one(const StepLaunch &l, const StepArgs<CT> &a) {
 }
 
 // Staged kernel: one block per (x column, y column, z chunk), like the generic kernel.
-template <class ST, class CT, int TY>
+template <class ST, class CT, int TY, int NS, int MINB>
 cudaError_t launch_staged_one(const StepLaunch &l, const StepArgs<CT> &a) {
-  constexpr size_t smem = staged_smem_bytes<ST, CT, TY>();
-  auto *k = sc_step_staged<ST, CT, TY>;
+  constexpr size_t smem = staged_smem_bytes<ST, CT, TY, NS>();
+  auto *k = sc_step_staged<ST, CT, TY, NS, MINB>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  const dim3 grid(a.nx / 32, (a.ny + TY - 1) / TY, (a.nz + a.tile_z - 1) / a.tile_z);
+  const dim3 grid((a.nx + 31) / 32, (a.ny + TY - 1) / TY, (a.nz + a.tile_z - 1) / a.tile_z);
   k<<<grid, dim3(32, TY), smem, l.stream>>>(a);
   return cudaGetLastError();
 }
 
+// Instantiated staged configurations (tile_y, stages, blocks per SM):
+// (4, 1|2, 2|3) and, except for F64 storage, (8, 1|2, 1|2).
 template <class ST, class CT>
 cudaError_t launch_staged(const StepLaunch &l, const StepArgs<CT> &a) {
-  if (l.lattice != kD3Q19 || l.stencil != kE4 || a.nx % 32 != 0 || a.nx < 64) return cudaErrorInvalidValue;
-  if (l.tile_y == 4) return launch_staged_one<ST, CT, 4>(l, a);
+  if (l.lattice != kD3Q19 || l.stencil != kE4 || a.nx < 32 || a.nx % StagedGeom<ST, 4>::CE != 0)
+    return cudaErrorInvalidValue;
+  const int ns = l.stages, mb = l.blocks_per_sm;
+  if (l.tile_y == 4) {
+    if (ns == 2 && mb <= 2) return launch_staged_one<ST, CT, 4, 2, 2>(l, a);
+    if (ns == 2 && mb == 3) return launch_staged_one<ST, CT, 4, 2, 3>(l, a);
+    if (ns == 1 && mb <= 2) return launch_staged_one<ST, CT, 4, 1, 2>(l, a);
+    if (ns == 1 && mb == 3) return launch_staged_one<ST, CT, 4, 1, 3>(l, a);
+  }
   if constexpr (sizeof(ST) < 8) {
-    if (l.tile_y == 8) return launch_staged_one<ST, CT, 8>(l, a);
+    if (l.tile_y == 8) {
+      if (ns == 2 && mb <= 1) return launch_staged_one<ST, CT, 8, 2, 1>(l, a);
+      if (ns == 2 && mb == 2) return launch_staged_one<ST, CT, 8, 2, 2>(l, a);
+      if (ns == 1 && mb <= 1) return launch_staged_one<ST, CT, 8, 1, 1>(l, a);
+      if (ns == 1 && mb == 2) return launch_staged_one<ST, CT, 8, 1, 2>(l, a);
+    }
   }
   return cudaErrorInvalidValue;
 }
@@ -93,6 +107,35 @@ const void *batched_any(int lat, int sten, int ty, size_t *smem) {
   if (lat == kD3Q19 && sten == kE4) return batched_ty<kD3Q19, kE4, ST, CT>(ty, smem);
   if (lat == kD3Q19 && sten == kE6) return batched_ty<kD3Q19, kE6, ST, CT>(ty, smem);
   if (lat == kD2Q9 && sten == kE4) return batched_ty<kD2Q9, kE4, ST, CT>(ty, smem);
+  return nullptr;
+}
+
+template <class ST, class CT, int TY, int NS, int MINB>
+const void *batched_staged_one(size_t *smem) {
+  constexpr size_t bytes = staged_smem_bytes<ST, CT, TY, NS>();
+  auto *k = sc_step_staged_batched<ST, CT, TY, NS, MINB>;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)) != cudaSuccess) return nullptr;
+  *smem = bytes;
+  return reinterpret_cast<const void *>(k);
+}
+
+// Same configurations as launch_staged.
+template <class ST, class CT>
+const void *batched_staged_any(int ty, int ns, int mb, size_t *smem) {
+  if (ty == 4) {
+    if (ns == 2 && mb <= 2) return batched_staged_one<ST, CT, 4, 2, 2>(smem);
+    if (ns == 2 && mb == 3) return batched_staged_one<ST, CT, 4, 2, 3>(smem);
+    if (ns == 1 && mb <= 2) return batched_staged_one<ST, CT, 4, 1, 2>(smem);
+    if (ns == 1 && mb == 3) return batched_staged_one<ST, CT, 4, 1, 3>(smem);
+  }
+  if constexpr (sizeof(ST) < 8) {
+    if (ty == 8) {
+      if (ns == 2 && mb <= 1) return batched_staged_one<ST, CT, 8, 2, 1>(smem);
+      if (ns == 2 && mb == 2) return batched_staged_one<ST, CT, 8, 2, 2>(smem);
+      if (ns == 1 && mb <= 1) return batched_staged_one<ST, CT, 8, 1, 1>(smem);
+      if (ns == 1 && mb == 2) return batched_staged_one<ST, CT, 8, 1, 2>(smem);
+    }
+  }
   return nullptr;
 }
 

@@ -28,10 +28,13 @@
 namespace scgb {
 
 // Pull the Q population pairs arriving at site (gx, gy, gz) and return their
-// sum (the density deviations); values go to v[] when V is true.
+// sum (the density deviations); values go to v[] when V is true.  Values are
+// deviations from w_i nbar; with a local reference the source site's density
+// nsrc[s] enters as w_i (nsrc[s] - nbar).
 template <int LAT, class ST, class CT, bool V>
 __device__ __forceinline__ P2<CT> pull_site(const ST *__restrict__ src, int gx, int gy, int gz, int nx, int ny,
-                                            int nz, int64_t N, const P2<CT> *inv_scale, P2<CT> *v) {
+                                            int nz, int64_t N, P2<CT> inv_scale, P2<CT> *v,
+                                            const float2 *__restrict__ nsrc = nullptr, P2<CT> nbar = P2<CT>()) {
   using L = Lattice<LAT>;
   // source coordinate for velocity component c is g - c
   const int X[3] = {wrapi(gx + 1, nx), gx, wrapi(gx - 1, nx)};
@@ -42,7 +45,11 @@ __device__ __forceinline__ P2<CT> pull_site(const ST *__restrict__ src, int gx, 
   for (int i = 0; i < L::Q; ++i) {
     const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
     const int site = X[cx + 1] + nx * (Y[cy + 1] + ny * Z[cz + 1]);
-    const P2<CT> g = Codec2<ST, CT>::template load<false>(src + ((int64_t)i * N + site) * 2, inv_scale[i]);
+    P2<CT> g = Codec2<ST, CT>::template load<false>(src + ((int64_t)i * N + site) * 2, inv_scale);
+    if constexpr (local_ref<ST>()) {
+      const float2 ns = __ldg(nsrc + site);
+      g = pfma(pbc(CT(L::w(i))), psub(pset(CT(ns.x), CT(ns.y)), nbar), g);
+    }
     if (V) v[i] = g;
     sum = padd(sum, g);
   }
@@ -186,11 +193,19 @@ __device__ __forceinline__ void check_density(const StepArgs<CT> &a, P2<CT> n) {
   if (!finite || (a.self_on && a.psi_exp && !positive)) atomicOr(a.err, 1u);
 }
 
-template <class ST, class CT, int Q>
+// Store the post-collision pairs (deviations from w_i nbar).  With a local
+// reference the stored value is relative to this site's density n = nbar + dn,
+// i.e. out_i - w_i dn, and n goes to ndst.
+template <int LAT, class ST, class CT, int Q>
 __device__ __forceinline__ void store_pairs(const StepArgs<CT> &a, ST *__restrict__ dst, int64_t site,
-                                            const P2<CT> (&out)[Q]) {
+                                            const P2<CT> (&out)[Q], P2<CT> n, P2<CT> dn) {
 #pragma unroll
-  for (int i = 0; i < Q; ++i) Codec2<ST, CT>::store(dst + ((int64_t)i * a.N + site) * 2, out[i], a.scale[i]);
+  for (int i = 0; i < Q; ++i) {
+    P2<CT> v = out[i];
+    if constexpr (local_ref<ST>()) v = pfma(pbc(CT(-Lattice<LAT>::w(i))), dn, v);
+    Codec2<ST, CT>::store(dst + ((int64_t)i * a.N + site) * 2, v, a.scale);
+  }
+  if constexpr (local_ref<ST>()) a.ndst[site] = make_float2(float(n.x), float(n.y));
 }
 
 // Collision of one site from its arriving population pairs g[i] and the ring.
@@ -213,7 +228,7 @@ __device__ __forceinline__ void collide_site(const StepArgs<CT> &a, const P2<CT>
   collide_pair<LAT, CT>(a, g, n, dn, u, F, out);
   if (valid) {
     check_density<CT>(a, n);
-    store_pairs<ST, CT, Q>(a, dst, site, out);
+    store_pairs<LAT, ST, CT, Q>(a, dst, site, out, n, dn);
   }
 }
 
@@ -253,7 +268,8 @@ __device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by
     const int gz = ((p % nz) + nz) % nz;
     // ---- density / psi deviations of this plane: own site
     {
-      const P2<CT> dn = pull_site<LAT, ST, CT, KEEP>(src, gx, gy, gz, nx, ny, nz, N, a.inv_scale, nxt);
+      const P2<CT> dn =
+          pull_site<LAT, ST, CT, KEEP>(src, gx, gy, gz, nx, ny, nz, N, a.inv_scale, nxt, a.nsrc, a.nbar);
       s_dn[slot * PLANE + own] = dn;
       if (a.self_on) s_psi[slot * PLANE + own] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp);
     }
@@ -270,7 +286,8 @@ __device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by
         px = c < H ? c - H : 32 + (c - H);
       }
       const int hx = ((x0 + px) % nx + nx) % nx, hy = ((y0 + py) % ny + ny) % ny;
-      const P2<CT> dn = pull_site<LAT, ST, CT, false>(src, hx, hy, gz, nx, ny, nz, N, a.inv_scale, nullptr);
+      const P2<CT> dn =
+          pull_site<LAT, ST, CT, false>(src, hx, hy, gz, nx, ny, nz, N, a.inv_scale, nullptr, a.nsrc, a.nbar);
       const int idx = (py + H) * SX + (px + H);
       s_dn[slot * PLANE + idx] = dn;
       if (a.self_on) s_psi[slot * PLANE + idx] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp);
@@ -288,7 +305,7 @@ __device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by
       if (HZ == 1) {
         collide_site<LAT, STEN, ST, CT, TY>(a, cur, s_dn, s_psi, sl, own, valid_xy, dst, site);
       } else {
-        if (!KEEP) pull_site<LAT, ST, CT, true>(src, gx, gy, gzc, nx, ny, nz, N, a.inv_scale, nxt);
+        if (!KEEP) pull_site<LAT, ST, CT, true>(src, gx, gy, gzc, nx, ny, nz, N, a.inv_scale, nxt, a.nsrc, a.nbar);
         collide_site<LAT, STEN, ST, CT, TY>(a, nxt, s_dn, s_psi, sl, own, valid_xy, dst, site);
       }
     }
@@ -319,6 +336,9 @@ __global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 16 / TY))
     const void *t = a.src;
     a.src = a.dst;
     a.dst = const_cast<void *>(t);
+    const float2 *u = a.nsrc;
+    a.nsrc = a.ndst;
+    a.ndst = const_cast<float2 *>(u);
   }
   step_block<LAT, STEN, ST, CT, TY>(a, it.y, it.z, it.w, smem_raw);
 }

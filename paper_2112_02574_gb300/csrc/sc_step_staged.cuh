@@ -1,8 +1,9 @@
-// The fused time step, staged variant (D3Q19, E4 stencil, nx % 32 == 0,
-// nx >= 64).  Same arithmetic as sc_step_kernel (shared collide_site and the
-// same summation order), different data movement:
+// The fused time step, staged variant (D3Q19, E4 stencil, nx >= 32 and nx a
+// multiple of the sites in a 16-byte chunk).  Same arithmetic as sc_step_kernel
+// (shared collide_site and the same summation order), different data movement:
 //
-//  * A block owns a column of 32 x TY sites in x-y and tile_z planes in z
+//  * A block owns a column of 32 x TY sites in x-y (the last x tile may be
+//    partial) and tile_z planes in z
 //    (blocks in x, y, z-chunk order, so neighbouring columns run together and
 //    the rows they share are L2 hits) and marches along z.
 //  * For every plane z the block needs, per direction i, the source rows
@@ -32,6 +33,7 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 template <class ST, int TY>
 struct StagedGeom {
@@ -46,59 +48,86 @@ struct StagedGeom {
   static constexpr int NHALO = PLANE - 32 * TY;
   static constexpr int NCH = WX / CE;              // chunks per row window
   static constexpr int NROW = Q * RY;              // row windows per plane
+  // local-reference densities (FP32 pairs, 16-bit storage only): a ring of NPLN
+  // planes, each rows y0-2 .. y0+TY+1 over the x window [x0 - 2, x0 + 34)
+  static constexpr bool LOCAL = local_ref<ST>();
+  static constexpr int RYN = TY + 4, OFFN = 2, WXN = 36, NCHN = 18;
+  static constexpr int NPLN = LOCAL ? 4 : 0;
+  static constexpr int NPLANE_N = RYN * WXN;  // float2 per ring plane
+  // shared-memory carve-up (bytes): NS population stages, the reference-density
+  // ring, per-plane row source pointers, row bases, row c^z, then the density / psi rings
+  static_assert(STAGE_BYTES % 16 == 0 && NPLANE_N % 2 == 0 && NROW % 2 == 0, "16-byte aligned regions");
+  template <int NS> __host__ __device__ static constexpr size_t at_nstage() { return NS * size_t(STAGE_BYTES); }
+  template <int NS> __host__ __device__ static constexpr size_t at_rowsrc() { return at_nstage<NS>() + sizeof(float2) * NPLN * NPLANE_N; }
+  template <int NS> __host__ __device__ static constexpr size_t at_rowbase() { return at_rowsrc<NS>() + sizeof(void *) * NROW; }
+  template <int NS> __host__ __device__ static constexpr size_t at_rowcz() { return at_rowbase<NS>() + sizeof(int64_t) * NROW; }
+  template <int NS> __host__ __device__ static constexpr size_t at_ring() { return at_rowcz<NS>() + sizeof(int) * ((NROW + 3) & ~3); }
 };
 
-// Shared memory: two stages, per-plane row source pointers, row tables, density / psi rings.
-template <class ST, class CT, int TY>
+// Shared memory of one block (the carve-up above, for NS population stages, plus
+// two rings of NPL planes).
+template <class ST, class CT, int TY, int NS>
 constexpr size_t staged_smem_bytes() {
   using G = StagedGeom<ST, TY>;
-  return 2 * size_t(G::STAGE_BYTES) + sizeof(int64_t) * 2 * G::NROW + sizeof(int) * ((G::NROW + 3) & ~3) +
-         sizeof(P2<CT>) * 2 * G::NPL * G::PLANE;
+  return G::template at_ring<NS>() + sizeof(P2<CT>) * 2 * G::NPL * G::PLANE;
 }
 
 // Sum of the Q staged population pairs arriving at tile position (px, py), in
 // direction order (identical to pull_site's order); values go to v[] when V is true.
+// With a local reference, nring + nsl[1 - c^z] is the density plane of the source
+// plane z - c^z.
 template <class ST, class CT, int TY, bool V>
-__device__ __forceinline__ P2<CT> staged_sum(const ST *stage, int px, int py, const P2<CT> *inv_scale, P2<CT> *v) {
+__device__ __forceinline__ P2<CT> staged_sum(const ST *stage, const float2 *nring, const int (&nsl)[3], int px,
+                                             int py, P2<CT> inv_scale, P2<CT> *v, P2<CT> nbar) {
   using G = StagedGeom<ST, TY>;
   using L = Lattice<kD3Q19>;
   const ST *base = stage + ((py + 1) * G::WX + px + G::OFF) * 2;
   P2<CT> sum = pbc(CT(0));
 #pragma unroll
   for (int i = 0; i < G::Q; ++i) {
-    const P2<CT> g =
-        Codec2<ST, CT>::template load<true>(base + (i * G::RY * G::WX - L::c(i, 0)) * 2, inv_scale[i]);
+    P2<CT> g = Codec2<ST, CT>::template load<true>(base + (i * G::RY * G::WX - L::c(i, 0)) * 2, inv_scale);
+    if constexpr (G::LOCAL) {
+      // density of the source site (x - c_i, y - c_i^y, plane z - c_i^z)
+      const float2 ns = nring[nsl[1 - L::c(i, 2)] + (py - L::c(i, 1) + 2) * G::WXN + px + G::OFFN - L::c(i, 0)];
+      g = pfma(pbc(CT(L::w(i))), psub(pset(CT(ns.x), CT(ns.y)), nbar), g);
+    }
     if (V) v[i] = g;
     sum = padd(sum, g);
   }
   return sum;
 }
 
-template <class ST, class CT, int TY>
-__global__ void __launch_bounds__(32 * TY, 1) sc_step_staged(const StepArgs<CT> a) {
+// One block's column (bx, by) x z-chunk bz of the lattice described by a.
+// NS: pipeline stages (2: the copy of plane k + 2 overlaps sum k and collide k - 1;
+// 1: the copy of plane k + 1 overlaps collide k - 1 only, for half the stage memory).
+// Window x coordinates wrap once: every chunk start lies in [-nx, 2 nx) for nx >= 32.
+template <class ST, class CT, int TY, int NS>
+__device__ __forceinline__ void staged_block(const StepArgs<CT> &a, int bx, int by, int bz,
+                                             unsigned char *smem_raw) {
+  static_assert(NS == 1 || NS == 2, "one or two pipeline stages");
   using G = StagedGeom<ST, TY>;
   using L = Lattice<kD3Q19>;
   constexpr int Q = G::Q;
   constexpr int NT = 32 * TY;
   constexpr int NTASK = (G::NHALO + NT - 1) / NT;  // halo sums per thread and plane
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  ST *stage0 = reinterpret_cast<ST *>(smem_raw);                                       // [2][STAGE_ELEMS]
-  const ST **rowsrc = reinterpret_cast<const ST **>(smem_raw + 2 * G::STAGE_BYTES);    // [NROW] this plane's rows
-  int64_t *rowbase = reinterpret_cast<int64_t *>(rowsrc + G::NROW);                    // [NROW]
-  int *rowcz = reinterpret_cast<int *>(rowbase + G::NROW);                             // [NROW]
-  P2<CT> *s_dn = reinterpret_cast<P2<CT> *>(rowcz + ((G::NROW + 3) & ~3));           // [NPL][PLANE]
-  P2<CT> *s_psi = s_dn + G::NPL * G::PLANE;                                            // [NPL][PLANE]
+  ST *stage0 = reinterpret_cast<ST *>(smem_raw);                                // [NS][STAGE_ELEMS]
+  float2 *nring = reinterpret_cast<float2 *>(smem_raw + G::template at_nstage<NS>());         // [NPLN][RYN][WXN]
+  const ST **rowsrc = reinterpret_cast<const ST **>(smem_raw + G::template at_rowsrc<NS>());  // [NROW]
+  int64_t *rowbase = reinterpret_cast<int64_t *>(smem_raw + G::template at_rowbase<NS>());    // [NROW]
+  int *rowcz = reinterpret_cast<int *>(smem_raw + G::template at_rowcz<NS>());                // [NROW]
+  P2<CT> *s_dn = reinterpret_cast<P2<CT> *>(smem_raw + G::template at_ring<NS>());            // [NPL][PLANE]
+  P2<CT> *s_psi = s_dn + G::NPL * G::PLANE;                                     // [NPL][PLANE]
 
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const int64_t plane_elems = (int64_t)nx * ny;
   const ST *__restrict__ src = static_cast<const ST *>(a.src);
   ST *__restrict__ dst = static_cast<ST *>(a.dst);
-  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * TY, z0 = blockIdx.z * a.tile_z;
+  const int x0 = bx * 32, y0 = by * TY, z0 = bz * a.tile_z;
   const int zend = min(z0 + a.tile_z, nz);
   const int np = zend - z0 + 2;  // planes z0 - 1 .. zend
   const int own = (ty + 1) * G::SX + (tx + 1);
-  const bool valid_xy = (y0 + ty < ny);  // x tiles are full (nx % 32 == 0)
+  const bool valid_xy = (x0 + tx < nx) && (y0 + ty < ny);
   const int gx = x0 + tx, gy = (y0 + ty) % ny;
 
   // row tables of this column: row = i * RY + r holds the source row
@@ -158,42 +187,70 @@ __global__ void __launch_bounds__(32 * TY, 1) sc_step_staged(const StepArgs<CT> 
       cp_async16(stage + (row * G::WX + c * G::CE) * 2, rowsrc[row] + (int64_t)xs * 2);
     }
   };
-  __syncthreads();
-  rows_for(wrapz(z0 - 1));
-  __syncthreads();
-  copy_rows(0);
-  cp_async_commit();
-  __syncthreads();
-  rows_for(wrapz(z0));
-  __syncthreads();
-  copy_rows(1);
-  cp_async_commit();
+  // local reference: density plane m (z = z0 - 2 + m, m = 0 .. np + 1) into ring slot m & 3
+  auto copy_nref = [&](int m) {
+    if constexpr (G::LOCAL) {
+      float2 *dstp = nring + (m & (G::NPLN - 1)) * G::NPLANE_N;
+      const int64_t zo = (int64_t)((((z0 - 2 + m) % nz) + nz) % nz) * ny;  // m - 2 can wrap more than once for nz < 3
+      for (int t = tid; t < G::RYN * G::NCHN; t += NT) {
+        const int rr = t / G::NCHN, c = t - rr * G::NCHN;
+        int ys = y0 - 2 + rr;
+        ys = ((ys % ny) + ny) % ny;
+        int xs = x0 - G::OFFN + 2 * c;
+        xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+        cp_async16(dstp + rr * G::WXN + 2 * c, a.nsrc + (zo + ys) * nx + xs);
+      }
+    }
+  };
+  // commit groups: {plane 0, densities 0-2}, {plane 1, density 3} (two stages), then
+  // per body k {plane k + NS, density k + NS + 2}: a group that completes plane p also
+  // completes the densities p .. p + 2 its sums read
+#pragma unroll
+  for (int j = 0; j < NS; ++j) {
+    __syncthreads();
+    rows_for(wrapz(z0 - 1 + j));
+    __syncthreads();
+    copy_rows(j);
+    if (j == 0) {
+      copy_nref(0);
+      copy_nref(1);
+    }
+    copy_nref(j + 2);
+    cp_async_commit();
+  }
 
   // one plane of the march: sum plane k (own population pairs into `mine`),
   // then collide plane k - 1 from `prev`
   auto body = [&](int k, P2<CT> (&prev)[Q], P2<CT> (&mine)[Q]) {
-    const int s = k & 1;
+    const int s = NS == 2 ? (k & 1) : 0;
     const ST *stage = stage0 + s * G::STAGE_ELEMS;
-    cp_async_wait_one();  // all groups but the newest (plane k + 1) are complete: plane k is in
-    __syncthreads();      // ... and visible to every thread; the last copy pass is over
-    if (k + 2 < np) rows_for(wrapz(z0 + 1 + k));
+    // density planes of z - 1, z, z + 1 (z = z0 - 1 + k, ring positions k .. k + 2)
+    const int nsl[3] = {(k & 3) * G::NPLANE_N, ((k + 1) & 3) * G::NPLANE_N, ((k + 2) & 3) * G::NPLANE_N};
+    if constexpr (NS == 2)
+      cp_async_wait_one();  // all groups but the newest (plane k + 1) are complete: plane k is in
+    else
+      cp_async_wait_all();
+    __syncthreads();  // ... and visible to every thread; the last copy pass is over
+    if (k + NS < np) rows_for(wrapz(z0 - 1 + k + NS));
     const int slot = k & (G::NPL - 1);
     {
-      const P2<CT> dn = staged_sum<ST, CT, TY, true>(stage, tx, ty, a.inv_scale, mine);
+      const P2<CT> dn = staged_sum<ST, CT, TY, true>(stage, nring, nsl, tx, ty, a.inv_scale, mine, a.nbar);
       s_dn[slot * G::PLANE + own] = dn;
       if (a.self_on) s_psi[slot * G::PLANE + own] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp);
     }
 #pragma unroll
     for (int m = 0; m < NTASK; ++m) {
       if (task_on[m]) {
-        const P2<CT> dn = staged_sum<ST, CT, TY, false>(stage, task_px[m], task_py[m], a.inv_scale, nullptr);
+        const P2<CT> dn =
+            staged_sum<ST, CT, TY, false>(stage, nring, nsl, task_px[m], task_py[m], a.inv_scale, nullptr, a.nbar);
         s_dn[slot * G::PLANE + task_idx[m]] = dn;
         if (a.self_on) s_psi[slot * G::PLANE + task_idx[m]] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp);
       }
     }
-    __syncthreads();  // stage s fully read, ring plane and next row pointers written
-    if (k + 2 < np) copy_rows(s);
-    cp_async_commit();  // (possibly empty) group for plane k + 2 keeps "newest = next plane"
+    __syncthreads();  // stage s and density slot (k + NS + 2) & 3 fully read, ring plane and row pointers written
+    if (k + NS < np) copy_rows(s);
+    if (k + NS + 2 <= np + 1) copy_nref(k + NS + 2);
+    cp_async_commit();  // (possibly empty) group for plane k + NS keeps "newest = plane k + NS"
     if (k >= 2) {
       const int sl[3] = {(slot + 2) & 3, (slot + 3) & 3, slot};  // planes k-2, k-1, k
       const int c = z0 - 2 + k;
@@ -208,6 +265,39 @@ __global__ void __launch_bounds__(32 * TY, 1) sc_step_staged(const StepArgs<CT> 
     body(k + 1, A, B);
   }
   if (k < np) body(k, B, A);
+}
+
+// MINB: resident blocks per SM the register allocation must allow.
+template <class ST, class CT, int TY, int NS, int MINB>
+__global__ void __launch_bounds__(32 * TY, MINB) sc_step_staged(const StepArgs<CT> a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  staged_block<ST, CT, TY, NS>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+}
+
+// Batched form (see sc_step_batched): block b works on items[b] = (lattice, bx,
+// by, bz) with the arguments args[lattice], source and destination swapped when
+// swap != 0.
+template <class ST, class CT, int TY, int NS, int MINB>
+__global__ void __launch_bounds__(32 * TY, MINB)
+    sc_step_staged_batched(const StepArgs<CT> *__restrict__ args, const int4 *__restrict__ items, int swap) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  // the lattice's arguments live in shared memory (read where used, not held in registers)
+  __shared__ StepArgs<CT> s_a;
+  const int4 it = items[blockIdx.x];
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    StepArgs<CT> a = args[it.x];
+    if (swap) {
+      const void *t = a.src;
+      a.src = a.dst;
+      a.dst = const_cast<void *>(t);
+      const float2 *u = a.nsrc;
+      a.nsrc = a.ndst;
+      a.ndst = const_cast<float2 *>(u);
+    }
+    s_a = a;
+  }
+  __syncthreads();
+  staged_block<ST, CT, TY, NS>(s_a, it.y, it.z, it.w, smem_raw);
 }
 
 }  // namespace scgb

@@ -1,8 +1,9 @@
 """Autotuner for the step kernel's block shape.
 
-Times sc_step for each candidate (variant, tile_y, tile_z) on the given
-lattice with CUDA events and returns the fastest.  The step kernels compute
-the same numbers for every tile shape (bitwise), so tuning changes speed only.
+Times sc_step for each candidate (variant, tile_y, tile_z, stages,
+blocks_per_sm) on the given lattice with CUDA events and returns the fastest.
+The step kernels compute the same numbers for every candidate (bitwise), so
+tuning changes speed only.
 """
 from __future__ import annotations
 
@@ -10,8 +11,9 @@ import torch
 
 from . import binding as B
 
-STAGED = [(2, 4, 8), (2, 4, 16), (2, 4, 32), (2, 8, 8), (2, 8, 16)]
-GENERIC = [(1, 4, 16), (1, 4, 32), (1, 8, 16), (1, 8, 32), (1, 2, 32)]
+STAGED = [(2, 4, 16, 2, 2), (2, 4, 16, 2, 3), (2, 4, 16, 1, 2), (2, 4, 16, 1, 3), (2, 4, 32, 1, 3),
+          (2, 4, 8, 1, 3), (2, 8, 16, 2, 1), (2, 8, 16, 1, 2)]
+GENERIC = [(1, 4, 16, 0, 0), (1, 4, 32, 0, 0), (1, 8, 16, 0, 0), (1, 8, 32, 0, 0), (1, 2, 32, 0, 0)]
 
 
 def staged_eligible(params) -> bool:
@@ -20,16 +22,18 @@ def staged_eligible(params) -> bool:
 
 
 def tune_step(params, nA0, nB0, candidates=None, steps: int = 64, warmup: int = 8, device="cuda"):
-    """Returns ((variant, tile_y, tile_z), ms_per_step, table) for the fastest candidate."""
+    """Returns ((variant, tile_y, tile_z, stages, blocks_per_sm), ms_per_step, table) for the
+    fastest candidate."""
     if candidates is None:
         candidates = (STAGED if staged_eligible(params) else []) + GENERIC
     if params.storage == B.SC_STORE_F64:
         candidates = [c for c in candidates if not (c[0] == 2 and c[1] != 4)]
     table = []
-    for variant, ty, tz in candidates:
+    for variant, ty, tz, ns, mb in candidates:
         p = B.make_params((params.nx, params.ny, params.nz), lattice=params.lattice, stencil=params.stencil,
                           psi_self=params.psi_self, storage=params.storage, tau=tuple(params.tau), G=params.G,
-                          G_self=tuple(params.G_self), tile_y=ty, tile_z=tz, variant=variant)
+                          G_self=tuple(params.G_self), tile_y=ty, tile_z=tz, variant=variant, stages=ns,
+                          blocks_per_sm=mb)
         sim = B.Simulation(p, nA0, nB0, device=device)
         sim.step(warmup)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -38,30 +42,33 @@ def tune_step(params, nA0, nB0, candidates=None, steps: int = 64, warmup: int = 
         b.record(sim.stream)
         b.synchronize()
         sim.sync()
-        table.append(((variant, ty, tz), a.elapsed_time(b) / steps))
+        table.append(((variant, ty, tz, ns, mb), a.elapsed_time(b) / steps))
         del sim
     best = min(table, key=lambda t: t[1])
     return best[0], best[1], table
 
 
-def tune_batch_tile_y(params_list, fields, candidates=(2, 4, 8), steps: int = 32, device="cuda"):
-    """tile_y for a batch (shared by its members), timed on the whole batch."""
+def with_config(p, cfg):
+    """Copy of sc_params p with (tile_y, tile_z, stages, blocks_per_sm) = cfg."""
+    ty, tz, ns, mb = cfg
+    return B.make_params((p.nx, p.ny, p.nz), lattice=p.lattice, stencil=p.stencil, psi_self=p.psi_self,
+                         storage=p.storage, tau=tuple(p.tau), G=p.G, G_self=tuple(p.G_self), tile_y=ty, tile_z=tz,
+                         variant=p.variant, stages=ns, blocks_per_sm=mb)
+
+
+def tune_batch(params_list, fields, candidates, steps: int = 32, device="cuda"):
+    """(tile_y, tile_z, stages, blocks_per_sm) for a batch (shared by its members), timed on the
+    whole batch.  Returns (best, ms_per_step, table)."""
     table = []
-    for ty in candidates:
-        plist = []
-        for p in params_list:
-            q = B.make_params((p.nx, p.ny, p.nz), lattice=p.lattice, stencil=p.stencil, psi_self=p.psi_self,
-                              storage=p.storage, tau=tuple(p.tau), G=p.G, G_self=tuple(p.G_self), tile_y=ty,
-                              tile_z=p.tile_z, variant=1)
-            plist.append(q)
-        batch = B.Batch(plist, fields, device=device)
+    for cfg in candidates:
+        batch = B.Batch([with_config(p, cfg) for p in params_list], fields, device=device)
         batch.step(4)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(batch.stream)
         batch.step(steps)
         b.record(batch.stream)
         b.synchronize()
-        table.append((ty, a.elapsed_time(b) / steps))
+        table.append((tuple(cfg), a.elapsed_time(b) / steps))
         del batch
     best = min(table, key=lambda t: t[1])
     return best[0], best[1], table

@@ -31,7 +31,8 @@ def test_workspace_bytes_layout(B):
     assert ws >= pops + 4 * 8 * 128**3
     assert ws % 256 == 0
     p16 = B.make_params((128, 128, 128), storage=B.SC_STORE_F16)
-    assert B.sc_workspace_bytes(p16) < ws
+    # 16-bit pairs plus one FP32 reference-density pair per site in each of the two buffers
+    assert B.sc_workspace_bytes(p16) - ws == 2 * 2 * 19 * 128**3 * 2 - pops + 2 * 8 * 128**3
 
 
 @pytest.mark.parametrize("bad", [
@@ -44,6 +45,9 @@ def test_workspace_bytes_layout(B):
     dict(shape=(4, 4, 4), storage=9),
     dict(shape=(4, 4, 4), tile_y=3),
     dict(shape=(4, 4, 4), G=float("inf")),
+    dict(shape=(64, 4, 4), stages=3),
+    dict(shape=(64, 4, 4), tile_y=4, blocks_per_sm=1),
+    dict(shape=(64, 4, 4), tile_y=8, blocks_per_sm=3),
 ])
 def test_invalid_parameters_rejected(B, bad):
     shape = bad.pop("shape")

@@ -53,7 +53,9 @@ def rel(a, b):
 
 CASES = [
     # (shape, lattice, stencil, psi, G_self) -- every shape spans >1 tile in x and y with a ragged tail;
-    # (64, 21, 19) and (96, 10, 7) take the TMA-staged kernel (nx % 32 == 0), the others the generic one
+    # by default the D3Q19 / E4 shapes take the staged kernel where nx >= 32 is a multiple of the
+    # storage's chunk sites (FP64: any nx, so also the partial x tiles of nx = 37 and 70), the others
+    # the generic one
     ((64, 21, 19), 1, 0, 1, (-0.4, 0.0)),
     ((96, 10, 7), 1, 0, 0, (0.0, 0.0)),
     ((37, 11, 19), 1, 0, 1, (-0.4, 0.0)),
@@ -131,19 +133,61 @@ def test_tiling_does_not_change_results(B, storage):
 
 @pytest.mark.parametrize("storage", ["F32", "F16", "BF16", "F64"])
 def test_staged_kernel_equals_generic_bitwise(B, storage):
-    """The TMA-staged kernel moves data differently but sums and collides in the
-    same order as the generic kernel: the states agree bit for bit."""
+    """The cp.async-staged kernel moves data differently but sums and collides in
+    the same order as the generic kernel: the states agree bit for bit for every
+    tile shape, pipeline depth and register budget."""
     st = getattr(B, f"SC_STORE_{storage}")
     outs = []
-    for variant, ty, tz in ((1, 4, 5), (2, 4, 3), (2, 8 if storage != "F64" else 4, 7)):
+    configs = [(1, 4, 5, 0, 0), (2, 4, 3, 2, 2), (2, 4, 3, 1, 3), (2, 4, 7, 2, 3), (2, 4, 1, 1, 2)]
+    if storage != "F64":
+        configs += [(2, 8, 7, 2, 1), (2, 8, 2, 1, 2), (2, 8, 13, 2, 2), (2, 8, 5, 1, 1)]
+    for variant, ty, tz, ns, mb in configs:
         sim2 = B.Simulation(B.make_params((96, 19, 13), psi_self=1, storage=st, tau=(1.0, 0.9), G=2.5,
-                                          G_self=(-0.4, 0.1), tile_y=ty, tile_z=tz, variant=variant),
+                                          G_self=(-0.4, 0.1), tile_y=ty, tile_z=tz, variant=variant, stages=ns,
+                                          blocks_per_sm=mb),
                             *S.droplet((13, 19, 96), (48, 9, 6), 3.25, n_in=0.85, n_out=0.15, amplitude=1e-3))
         sim2.step(9)
         sim2.sync()
         outs.append(sim2.state().cpu().numpy())
     for o in outs[1:]:
         np.testing.assert_array_equal(o, outs[0])
+
+
+@pytest.mark.parametrize("storage", ["F32", "F16", "BF16", "F64"])
+@pytest.mark.parametrize("nx", [32, 36, 44, 100])
+def test_staged_partial_x_tiles_equal_generic(B, storage, nx):
+    """Partial last x tile (nx not a multiple of 32) and a single tile narrower
+    than the copy window: the staged kernel's per-chunk periodic wrap gives the
+    generic kernel's state bit for bit."""
+    st = getattr(B, f"SC_STORE_{storage}")
+    shape = (nx, 11, 6)
+    outs = []
+    for variant in (1, 2):
+        sim = B.Simulation(B.make_params(shape, psi_self=1, storage=st, G=2.5, G_self=(-0.4, 0.1), tau=(1.0, 0.8),
+                                         tile_z=4, variant=variant),
+                           *S.droplet(shape[::-1], (nx // 2, 5, 3), 3.0, n_in=0.85, n_out=0.15, amplitude=1e-3))
+        sim.step(6)
+        sim.sync()
+        outs.append(sim.state().cpu().numpy())
+    np.testing.assert_array_equal(outs[1], outs[0])
+
+
+@pytest.mark.parametrize("storage", ["F32", "F16"])
+@pytest.mark.parametrize("nz", [1, 2, 3])
+def test_staged_thin_z_equals_generic(B, storage, nz):
+    """Periodic wrap of the staged kernel's plane windows when the box is thinner
+    than the z reach of a block (nz < 3): same state as the generic kernel."""
+    st = getattr(B, f"SC_STORE_{storage}")
+    shape = (64, 9, nz)
+    outs = []
+    for variant in (1, 2):
+        sim = B.Simulation(B.make_params(shape, psi_self=1, storage=st, G=2.5, G_self=(-0.4, 0.0), tile_y=4,
+                                         tile_z=2, variant=variant),
+                           *S.droplet(shape[::-1], (32, 4, 0), 3.0, n_in=0.85, n_out=0.15, amplitude=1e-3))
+        sim.step(7)
+        sim.sync()
+        outs.append(sim.state().cpu().numpy())
+    np.testing.assert_array_equal(outs[1], outs[0])
 
 
 def test_swap_symmetry_bitwise(B):
