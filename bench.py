@@ -38,7 +38,13 @@ BYTES_PER_SITE = {"f32": 304, "f16": 168, "bf16": 168, "f64": 608}
 # still hash to the captured version.
 KERNEL_SOURCES = ["paper_2112_02574_gb300/csrc/sc_common.cuh", "paper_2112_02574_gb300/csrc/sc_step_kernel.cuh",
                   "paper_2112_02574_gb300/csrc/sc_step_staged.cuh"]
-MEASURED_TRAFFIC = {("aac010c37336a0b0", "f32"): 624.268032e6}
+# DRAM bytes per step launch (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture), keyed by the
+# kernel sources' hash, the storage and the launch (tile_y, stages, blocks_per_sm, blocks); a change to any of
+# them drops the figure (reported as null) until it is measured again
+MEASURED_TRAFFIC = {
+    ("3d57a13b14e25978", "f32", "v2 ty4 ns2 mb2 g608"): 618.647296e6,
+    ("3d57a13b14e25978", "f16", "v2 ty8 ns1 mb2 g304"): 329.957888e6,
+}
 
 
 def workload_config(storage: str):
@@ -114,6 +120,10 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def traffic_key(cfg) -> str:
+    return "v{variant} ty{tile_y} ns{stages} mb{blocks_per_sm} g{blocks}".format(**cfg)
 
 
 def kernel_hash() -> str:
@@ -245,6 +255,7 @@ def run_gpu(args, rank, world, local_rank):
     sites = SHAPE[0] * SHAPE[1] * SHAPE[2]
     with torch.cuda.stream(stream):
         sim = B.Simulation(params, nA0, nB0, device=dev, stream=stream)
+        step_cfg = sim.step_config
         rows = torch.empty(128 * 6, dtype=torch.float64, device=dev)
         pio = torch.empty(2, dtype=torch.float64, device=dev)
         sig = torch.empty(8, dtype=torch.float64, device=dev)
@@ -344,8 +355,9 @@ def run_gpu(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": storage, "data": "synthetic", "config": workload_config(storage),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": MEASURED_TRAFFIC.get((kernel_hash(), storage)) if args.variant != 1 else None,
-                     "kernel": "sc_step_staged" if args.variant != 1 else "sc_step_kernel",
+                     "traffic": MEASURED_TRAFFIC.get((kernel_hash(), storage, traffic_key(step_cfg))),
+                     "kernel": "sc_step_staged" if step_cfg["variant"] == 2 else "sc_step_kernel",
+                     "launch": step_cfg,
                      "bytes_per_site": BYTES_PER_SITE[storage], "algorithmic_bytes_per_launch": alg_bytes,
                      "kernel_ms": kern_ms, "peak_source": peak_kind},
         "hbm_roofline_mlups_frac": value / world * 1e6 * BYTES_PER_SITE[storage] / (peak * 1e9),

@@ -62,12 +62,13 @@ typedef enum { SC_PSI_N = 0, SC_PSI_EXP = 1 } sc_psi;
 /* Population storage.  F32/F64 store deviations g_i = f_i - w_i nbar_J from a
  * rest equilibrium with the mean initial density nbar_J.  F16/BF16 store the
  * deviation from each site's own rest equilibrium, (f*_i(s) - w_i n_J(s)) 2^k(J)
- * (F16: a power-of-two scale per component fixed at sc_create; BF16: unscaled), with n_J(s) -- the sum
- * of the values stored at s, i.e. the site's density when it was written --
- * kept beside them as an FP32 pair per site.  Collision arithmetic is FP32 for
- * F32/F16/BF16 and FP64 for F64.  In device memory the two components of a
+ * (F16: a power-of-two scale per component fixed at sc_create; BF16: unscaled),
+ * with n_J(s) the site's density when it was written (the sum of the values
+ * stored at s) and n_J(s) - nbar_J kept beside them as an FP32 pair per site.
+ * Collision arithmetic is FP32 for F32/F16/BF16 and FP64 for F64.  In device memory the two components of a
  * direction and site are adjacent ([i][site][J]); sc_get_state / sc_set_state
- * copy that buffer followed, for F16/BF16, by the [site][J] FP32 densities. */
+ * copy that buffer followed, for F16/BF16, by the [site][J] FP32 density
+ * deviations. */
 typedef enum { SC_STORE_F32 = 0, SC_STORE_F16 = 1, SC_STORE_BF16 = 2, SC_STORE_F64 = 3 } sc_storage;
 typedef enum { SC_PROFILE_RADIAL = 0, SC_PROFILE_PLANAR_Z = 1, SC_PROFILE_AXIS_X = 2 } sc_profile_kind;
 
@@ -80,7 +81,10 @@ typedef struct {
   int32_t psi_self;    /* sc_psi */
   int32_t storage;     /* sc_storage */
   int32_t tile_y;      /* step-kernel tile rows (1, 2, 4 or 8); 0 = library default */
-  int32_t tile_z;      /* planes per step-kernel work item (>= 1); 0 = library default */
+  int32_t tile_z;      /* planes per step-kernel work item (>= 1); 0 = library default
+                          (32; for the staged kernel on a lattice whose grid of 32-plane
+                          chunks would fill fewer than four waves of the GPU, a balanced
+                          split whose grid fills whole waves) */
   int32_t variant;     /* step kernel: 0 = automatic, 1 = generic (any size, any stencil),
                           2 = cp.async-staged (D3Q19, E4, nx % 32 == 0, nx >= 64,
                           tile_y 4 or 8; tile_y 4 for F64); both compute the same numbers */
@@ -225,6 +229,12 @@ int64_t sc_batch_launches(const sc_batch *batch);
 /* Step kernel of the batch: 1 generic, 2 staged (0 for NULL). */
 int32_t sc_batch_variant(const sc_batch *batch);
 void sc_batch_destroy(sc_batch *batch);
+
+/* The step kernel this context launches: out[0..8) = variant (1 generic, 2
+ * staged), tile_y, tile_z, stages, blocks_per_sm, blocks per launch, balanced
+ * split K (0: plain grid of tile_z chunks), columns with K + 1 chunks.  n: room
+ * in out (>= 8).  Host only, no synchronisation. */
+sc_status sc_step_config(const sc_ctx *ctx, int32_t *out, int32_t n);
 
 /* Number of step-kernel launches issued by this context so far. */
 int64_t sc_kernel_launches(const sc_ctx *ctx);

@@ -77,6 +77,7 @@ def _load():
         "sc_sync": (I32, [V]),
         "sc_run_host": (I32, [P, V, V, I64, V, V, V, Z, V]),
         "sc_kernel_launches": (I64, [V]),
+        "sc_step_config": (I32, [V, ctypes.POINTER(ctypes.c_int32), I32]),
         "sc_batch_workspace_bytes": (Z, [I32, P]),
         "sc_batch_create": (I32, [I32, P, ctypes.POINTER(V), ctypes.POINTER(V), V, Z, V, ctypes.POINTER(V)]),
         "sc_batch_step": (I32, [V, I64]),
@@ -244,6 +245,15 @@ def sc_kernel_launches(ctx) -> int:
     return lib.sc_kernel_launches(ctx)
 
 
+STEP_CONFIG_KEYS = ("variant", "tile_y", "tile_z", "stages", "blocks_per_sm", "blocks", "zsplit_k", "zsplit_rem")
+
+
+def sc_step_config(ctx) -> dict:
+    out = (ctypes.c_int32 * 8)()
+    _check(lib.sc_step_config(ctx, out, 8))
+    return dict(zip(STEP_CONFIG_KEYS, list(out)))
+
+
 def sc_reference_density(ctx):
     out = (ctypes.c_double * 2)()
     _check(lib.sc_reference_density(ctx, out))
@@ -335,6 +345,11 @@ class Simulation:
     @property
     def launches(self) -> int:
         return sc_kernel_launches(self.ctx)
+
+    @property
+    def step_config(self) -> dict:
+        """The step kernel this simulation launches (variant, tiles, split, blocks per launch)."""
+        return sc_step_config(self.ctx)
 
     @property
     def nbar(self):

@@ -65,8 +65,9 @@ bool staged_eligible(const sc_params *p, int tile_y) {
   return tile_y == 4 || tile_y == 8;
 }
 
-// Kernel choice and tiles (measured sweeps at 128^3 and 256^3 set the defaults).
-int staged_default_tile_y(const sc_params *p) { return p->storage == SC_STORE_F64 ? 4 : 8; }
+// Kernel choice and tiles (measured sweeps at 128^3, 256^3 and 512^3 set the defaults).
+bool is_16bit(int storage) { return storage == SC_STORE_F16 || storage == SC_STORE_BF16; }
+int staged_default_tile_y(const sc_params *p) { return is_16bit(p->storage) ? 8 : 4; }
 bool use_staged(const sc_params *p) {
   if (p->variant == 1) return false;
   return staged_eligible(p, p->tile_y ? p->tile_y : staged_default_tile_y(p));
@@ -79,7 +80,7 @@ int default_tile_y(const sc_params *p) {
 int effective_stages(const sc_params *p, int tile_y) { return p->stages ? p->stages : (tile_y == 8 ? 1 : 2); }
 int effective_blocks_per_sm(const sc_params *p, int tile_y) {
   if (p->blocks_per_sm) return p->blocks_per_sm;
-  return tile_y == 8 ? 2 : (p->storage == SC_STORE_F64 ? 2 : 3);
+  return tile_y == 8 ? 2 : (is_16bit(p->storage) ? 3 : 2);
 }
 int default_tile_z(const sc_params *p) {
   if (p->lattice == SC_D2Q9) return 1;
@@ -168,6 +169,7 @@ struct sc_ctx {
   int cur;  // buffer holding the current state
   int tile_y, tile_z;
   int staged, stages, blocks_per_sm;
+  int zbal_k, zbal_rem, zbal_cols, zbal_cols_x;  // balanced z split of the staged kernel (zbal_k > 0)
   double nbar[2], psibar[2];
   double scale[2][19], inv_scale[2][19];
   int64_t launches;
@@ -296,7 +298,49 @@ StepArgs<CT> step_args(sc_ctx *c) {
   a.err = status_word(c);
   a.nsrc = c->L.ref_bytes ? reinterpret_cast<const float2 *>(c->ws + c->L.off_ref[c->cur]) : nullptr;
   a.ndst = c->L.ref_bytes ? reinterpret_cast<float2 *>(c->ws + c->L.off_ref[1 - c->cur]) : nullptr;
+  a.zbal_k = c->zbal_k;
+  a.zbal_rem = c->zbal_rem;
+  a.zbal_cols = c->zbal_cols;
+  a.zbal_cols_x = c->zbal_cols_x;
   return a;
+}
+
+// Balanced z split of the staged kernel (tile_z left to the library, and a plain grid
+// of tile_z chunks would fill fewer than four waves of the GPU): the grid is
+// exactly waves x (SMs x resident blocks per SM) blocks, with waves chosen for
+// z-chunks of about kTargetChunk planes, and every column of 32 x tile_y sites is
+// cut into K or K + 1 equal z-chunks.  A fixed tile_z instead leaves a partly empty
+// last wave whenever the block count is not a multiple of the resident slots (at
+// 128^3: 256 blocks of 32 planes for 304 slots).
+sc_status plan_balanced_split(sc_ctx *c) {
+  constexpr int kTargetChunk = 24;
+  int dev = 0, sms = 0, occ = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) {
+    switch (c->p.storage) {
+      case SC_STORE_F32: e = staged_occupancy_f32(c->tile_y, c->stages, c->blocks_per_sm, &occ); break;
+      case SC_STORE_F16: e = staged_occupancy_f16(c->tile_y, c->stages, c->blocks_per_sm, &occ); break;
+      case SC_STORE_BF16: e = staged_occupancy_bf16(c->tile_y, c->stages, c->blocks_per_sm, &occ); break;
+      default: e = staged_occupancy_f64(c->tile_y, c->stages, c->blocks_per_sm, &occ); break;
+    }
+  }
+  if (e != cudaSuccess) return fail(SC_ECUDA, "occupancy of the staged kernel: %s", cudaGetErrorString(e));
+  const int64_t cols_x = (c->p.nx + 31) / 32, cols = cols_x * ((c->p.ny + c->tile_y - 1) / c->tile_y);
+  const int64_t nz = c->p.nz, slots = (int64_t)sms * (occ > 0 ? occ : 1);
+  const int64_t fixed_blocks = cols * ((nz + c->tile_z - 1) / c->tile_z);
+  if (fixed_blocks >= 4 * slots) return SC_OK;  // many waves: the plain grid's last-wave loss is small
+  int64_t waves = cols * nz / (slots * kTargetChunk);
+  if (waves < 1) waves = 1;
+  int64_t G = slots * waves;
+  const int64_t gmax = cols * (nz / 4 > 1 ? nz / 4 : 1);  // chunks of 4 planes or more
+  if (G > gmax) G = gmax;
+  if (G < cols || G > (int64_t(1) << 31) - 1) return SC_OK;  // more columns than slots: plain grid
+  c->zbal_k = (int)(G / cols);
+  c->zbal_rem = (int)(G % cols);
+  c->zbal_cols = (int)cols;
+  c->zbal_cols_x = (int)cols_x;
+  return SC_OK;
 }
 
 sc_status launch_one_step(sc_ctx *c) {
@@ -408,6 +452,13 @@ sc_status sc_create(const sc_params *params, const double *nA0, const double *nB
   c->stages = effective_stages(params, c->tile_y);
   c->blocks_per_sm = effective_blocks_per_sm(params, c->tile_y);
   c->fields_at = -1;
+  if (c->staged && params->tile_z == 0) {
+    st = plan_balanced_split(c);
+    if (st != SC_OK) {
+      delete c;
+      return st;
+    }
+  }
   double mean[2], maxdev[2];
   cudaError_t e = cudaMemsetAsync(c->ws + L.off_status, 0, kStatusBytes, c->stream);
   if (e != cudaSuccess) {
@@ -899,6 +950,18 @@ void sc_batch_destroy(sc_batch *b) {
     for (int k = 0; k < b->n; ++k) delete b->ctx[k];
   delete[] b->ctx;
   delete b;
+}
+
+sc_status sc_step_config(const sc_ctx *c, int32_t *out, int32_t n) {
+  if (!c || !out) return fail(SC_EINVAL, "ctx and out must be non-NULL");
+  if (n < 8) return fail(SC_EINVAL, "out must hold 8 values, got room for %d", n);
+  const int64_t grid = c->zbal_k > 0 ? (int64_t)c->zbal_k * c->zbal_cols + c->zbal_rem
+                                     : (int64_t)((c->p.nx + 31) / 32) * ((c->p.ny + c->tile_y - 1) / c->tile_y) *
+                                           ((c->p.nz + c->tile_z - 1) / c->tile_z);
+  const int32_t v[8] = {c->staged ? 2 : 1, c->tile_y, c->tile_z, c->staged ? c->stages : 0,
+                        c->staged ? c->blocks_per_sm : 0, (int32_t)grid, c->zbal_k, c->zbal_rem};
+  for (int k = 0; k < 8; ++k) out[k] = v[k];
+  return SC_OK;
 }
 
 int64_t sc_kernel_launches(const sc_ctx *c) { return c ? c->launches : 0; }

@@ -37,7 +37,7 @@ __device__ __forceinline__ void store_dev(ST *p, double v, double scale) {
 
 struct PopArgs {
   void *buf;         // stored populations [Q][N][2]
-  float2 *nref;      // local reference densities [N] (16-bit storage; nullptr otherwise)
+  float2 *nref;      // local reference density deviations n_ref - nbar [N] (16-bit storage; nullptr otherwise)
   int nx, ny, nz;
   int64_t N;
   double nbar[2];
@@ -49,7 +49,7 @@ struct PopArgs {
 template <int LAT, class ST>
 __device__ __forceinline__ double pop_value(const PopArgs &a, const ST *buf, int i, int J, int64_t s) {
   const double g = load_dev<ST>(buf + ((int64_t)i * a.N + s) * 2 + J, a.inv_scale[J][i]);
-  const double ref = local_ref<ST>() ? double(J == 0 ? a.nref[s].x : a.nref[s].y) : a.nbar[J];
+  const double ref = a.nbar[J] + (local_ref<ST>() ? double(J == 0 ? a.nref[s].x : a.nref[s].y) : 0.0);
   return g + Lattice<LAT>::w(i) * ref;
 }
 
@@ -103,12 +103,13 @@ __global__ void pop_kernel(PopArgs a, int mode, const double *n0A, const double 
           for (int i = 0; i < L::Q; ++i)
             sum += f[((int64_t)J * L::Q + i) * N + site_at(x + L::c(i, 0), y + L::c(i, 1), z + L::c(i, 2), a.nx, a.ny, a.nz)];
         }
-        ref[J] = double(float(sum));  // the reference is kept in FP32
+        ref[J] = a.nbar[J] + double(float(sum - a.nbar[J]));  // the deviation is kept in FP32
       } else {
         ref[J] = a.nbar[J];
       }
     }
-    if constexpr (local_ref<ST>()) a.nref[s] = make_float2(float(ref[0]), float(ref[1]));
+    if constexpr (local_ref<ST>())
+      a.nref[s] = make_float2(float(ref[0] - a.nbar[0]), float(ref[1] - a.nbar[1]));
 #pragma unroll
     for (int J = 0; J < 2; ++J)
 #pragma unroll

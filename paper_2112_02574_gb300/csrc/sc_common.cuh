@@ -226,10 +226,13 @@ struct StepArgs {
   P2<CT> inv_scale;  // 2^-k(J)
   unsigned int *err;     // device status word (bit 0: density out of range)
   // Local reference (F16/BF16 storage): the value stored at site s is
-  // (f*_i(s) - w_i n(s)) 2^k with n(s) the site's density when it was written,
-  // kept as an FP32 pair per site: read from nsrc, written to ndst.
+  // (f*_i(s) - w_i n(s)) 2^k with n(s) the site's density when it was written;
+  // n(s) - nbar is kept as an FP32 pair per site: read from nsrc, written to ndst.
   const float2 *nsrc;
   float2 *ndst;
+  // Balanced z split of the staged kernel (zbal_k > 0; 1-D grid of zbal_k * zbal_cols
+  // + zbal_rem blocks): zbal_cols = x tiles * y tiles, zbal_cols_x = x tiles.
+  int zbal_k, zbal_rem, zbal_cols, zbal_cols_x;
 };
 
 // Storage modes whose populations are deviations from each site's own density

@@ -9,3 +9,6 @@ const void *scgb::batched_kernel_bf16(int lattice, int stencil, int tile_y, size
 const void *scgb::batched_staged_kernel_bf16(int tile_y, int stages, int blocks_per_sm, size_t *smem) {
   return batched_staged_any<__nv_bfloat16, float>(tile_y, stages, blocks_per_sm, smem);
 }
+cudaError_t scgb::staged_occupancy_bf16(int tile_y, int stages, int blocks_per_sm, int *blocks) {
+  return staged_occupancy<__nv_bfloat16, float>(tile_y, stages, blocks_per_sm, blocks);
+}

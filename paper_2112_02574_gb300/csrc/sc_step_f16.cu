@@ -7,3 +7,6 @@ const void *scgb::batched_kernel_f16(int lattice, int stencil, int tile_y, size_
 const void *scgb::batched_staged_kernel_f16(int tile_y, int stages, int blocks_per_sm, size_t *smem) {
   return batched_staged_any<__half, float>(tile_y, stages, blocks_per_sm, smem);
 }
+cudaError_t scgb::staged_occupancy_f16(int tile_y, int stages, int blocks_per_sm, int *blocks) {
+  return staged_occupancy<__half, float>(tile_y, stages, blocks_per_sm, blocks);
+}

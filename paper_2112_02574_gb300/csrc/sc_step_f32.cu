@@ -7,3 +7,6 @@ const void *scgb::batched_kernel_f32(int lattice, int stencil, int tile_y, size_
 const void *scgb::batched_staged_kernel_f32(int tile_y, int stages, int blocks_per_sm, size_t *smem) {
   return batched_staged_any<float, float>(tile_y, stages, blocks_per_sm, smem);
 }
+cudaError_t scgb::staged_occupancy_f32(int tile_y, int stages, int blocks_per_sm, int *blocks) {
+  return staged_occupancy<float, float>(tile_y, stages, blocks_per_sm, blocks);
+}

@@ -33,13 +33,43 @@ cudaError_t launch_staged_one(const StepLaunch &l, const StepArgs<CT> &a) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  const dim3 grid((a.nx + 31) / 32, (a.ny + TY - 1) / TY, (a.nz + a.tile_z - 1) / a.tile_z);
+  const dim3 grid = a.zbal_k > 0 ? dim3(a.zbal_k * a.zbal_cols + a.zbal_rem)
+                                 : dim3((a.nx + 31) / 32, (a.ny + TY - 1) / TY, (a.nz + a.tile_z - 1) / a.tile_z);
   k<<<grid, dim3(32, TY), smem, l.stream>>>(a);
   return cudaGetLastError();
 }
 
+template <class ST, class CT, int TY, int NS, int MINB>
+cudaError_t staged_occupancy_one(int *blocks) {
+  constexpr size_t smem = staged_smem_bytes<ST, CT, TY, NS>();
+  auto *k = sc_step_staged<ST, CT, TY, NS, MINB>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, 32 * TY, smem);
+}
+
 // Instantiated staged configurations (tile_y, stages, blocks per SM):
 // (4, 1|2, 2|3) and, except for F64 storage, (8, 1|2, 1|2).
+// Resident blocks per SM of the staged kernel for (tile_y, stages, blocks_per_sm).
+template <class ST, class CT>
+cudaError_t staged_occupancy(int ty, int ns, int mb, int *blocks) {
+  if (ty == 4) {
+    if (ns == 2 && mb <= 2) return staged_occupancy_one<ST, CT, 4, 2, 2>(blocks);
+    if (ns == 2 && mb == 3) return staged_occupancy_one<ST, CT, 4, 2, 3>(blocks);
+    if (ns == 1 && mb <= 2) return staged_occupancy_one<ST, CT, 4, 1, 2>(blocks);
+    if (ns == 1 && mb == 3) return staged_occupancy_one<ST, CT, 4, 1, 3>(blocks);
+  }
+  if constexpr (sizeof(ST) < 8) {
+    if (ty == 8) {
+      if (ns == 2 && mb <= 1) return staged_occupancy_one<ST, CT, 8, 2, 1>(blocks);
+      if (ns == 2 && mb == 2) return staged_occupancy_one<ST, CT, 8, 2, 2>(blocks);
+      if (ns == 1 && mb <= 1) return staged_occupancy_one<ST, CT, 8, 1, 1>(blocks);
+      if (ns == 1 && mb == 2) return staged_occupancy_one<ST, CT, 8, 1, 2>(blocks);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
 template <class ST, class CT>
 cudaError_t launch_staged(const StepLaunch &l, const StepArgs<CT> &a) {
   if (l.lattice != kD3Q19 || l.stencil != kE4 || a.nx < 32 || a.nx % StagedGeom<ST, 4>::CE != 0)

@@ -30,11 +30,11 @@ namespace scgb {
 // Pull the Q population pairs arriving at site (gx, gy, gz) and return their
 // sum (the density deviations); values go to v[] when V is true.  Values are
 // deviations from w_i nbar; with a local reference the source site's density
-// nsrc[s] enters as w_i (nsrc[s] - nbar).
+// deviation nsrc[s] = n(s) - nbar enters as w_i nsrc[s].
 template <int LAT, class ST, class CT, bool V>
 __device__ __forceinline__ P2<CT> pull_site(const ST *__restrict__ src, int gx, int gy, int gz, int nx, int ny,
                                             int nz, int64_t N, P2<CT> inv_scale, P2<CT> *v,
-                                            const float2 *__restrict__ nsrc = nullptr, P2<CT> nbar = P2<CT>()) {
+                                            const float2 *__restrict__ nsrc = nullptr) {
   using L = Lattice<LAT>;
   // source coordinate for velocity component c is g - c
   const int X[3] = {wrapi(gx + 1, nx), gx, wrapi(gx - 1, nx)};
@@ -48,7 +48,7 @@ __device__ __forceinline__ P2<CT> pull_site(const ST *__restrict__ src, int gx, 
     P2<CT> g = Codec2<ST, CT>::template load<false>(src + ((int64_t)i * N + site) * 2, inv_scale);
     if constexpr (local_ref<ST>()) {
       const float2 ns = __ldg(nsrc + site);
-      g = pfma(pbc(CT(L::w(i))), psub(pset(CT(ns.x), CT(ns.y)), nbar), g);
+      g = pfma(pbc(CT(L::w(i))), pset(CT(ns.x), CT(ns.y)), g);
     }
     if (V) v[i] = g;
     sum = padd(sum, g);
@@ -195,7 +195,7 @@ __device__ __forceinline__ void check_density(const StepArgs<CT> &a, P2<CT> n) {
 
 // Store the post-collision pairs (deviations from w_i nbar).  With a local
 // reference the stored value is relative to this site's density n = nbar + dn,
-// i.e. out_i - w_i dn, and n goes to ndst.
+// i.e. out_i - w_i dn, and dn = n - nbar goes to ndst.
 template <int LAT, class ST, class CT, int Q>
 __device__ __forceinline__ void store_pairs(const StepArgs<CT> &a, ST *__restrict__ dst, int64_t site,
                                             const P2<CT> (&out)[Q], P2<CT> n, P2<CT> dn) {
@@ -205,7 +205,7 @@ __device__ __forceinline__ void store_pairs(const StepArgs<CT> &a, ST *__restric
     if constexpr (local_ref<ST>()) v = pfma(pbc(CT(-Lattice<LAT>::w(i))), dn, v);
     Codec2<ST, CT>::store(dst + ((int64_t)i * a.N + site) * 2, v, a.scale);
   }
-  if constexpr (local_ref<ST>()) a.ndst[site] = make_float2(float(n.x), float(n.y));
+  if constexpr (local_ref<ST>()) a.ndst[site] = make_float2(float(dn.x), float(dn.y));
 }
 
 // Collision of one site from its arriving population pairs g[i] and the ring.
@@ -269,7 +269,7 @@ __device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by
     // ---- density / psi deviations of this plane: own site
     {
       const P2<CT> dn =
-          pull_site<LAT, ST, CT, KEEP>(src, gx, gy, gz, nx, ny, nz, N, a.inv_scale, nxt, a.nsrc, a.nbar);
+          pull_site<LAT, ST, CT, KEEP>(src, gx, gy, gz, nx, ny, nz, N, a.inv_scale, nxt, a.nsrc);
       s_dn[slot * PLANE + own] = dn;
       if (a.self_on) s_psi[slot * PLANE + own] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp);
     }
@@ -287,7 +287,7 @@ __device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by
       }
       const int hx = ((x0 + px) % nx + nx) % nx, hy = ((y0 + py) % ny + ny) % ny;
       const P2<CT> dn =
-          pull_site<LAT, ST, CT, false>(src, hx, hy, gz, nx, ny, nz, N, a.inv_scale, nullptr, a.nsrc, a.nbar);
+          pull_site<LAT, ST, CT, false>(src, hx, hy, gz, nx, ny, nz, N, a.inv_scale, nullptr, a.nsrc);
       const int idx = (py + H) * SX + (px + H);
       s_dn[slot * PLANE + idx] = dn;
       if (a.self_on) s_psi[slot * PLANE + idx] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp);
@@ -305,7 +305,7 @@ __device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by
       if (HZ == 1) {
         collide_site<LAT, STEN, ST, CT, TY>(a, cur, s_dn, s_psi, sl, own, valid_xy, dst, site);
       } else {
-        if (!KEEP) pull_site<LAT, ST, CT, true>(src, gx, gy, gzc, nx, ny, nz, N, a.inv_scale, nxt, a.nsrc, a.nbar);
+        if (!KEEP) pull_site<LAT, ST, CT, true>(src, gx, gy, gzc, nx, ny, nz, N, a.inv_scale, nxt, a.nsrc);
         collide_site<LAT, STEN, ST, CT, TY>(a, nxt, s_dn, s_psi, sl, own, valid_xy, dst, site);
       }
     }

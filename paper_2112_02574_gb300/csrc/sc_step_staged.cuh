@@ -74,11 +74,11 @@ constexpr size_t staged_smem_bytes() {
 
 // Sum of the Q staged population pairs arriving at tile position (px, py), in
 // direction order (identical to pull_site's order); values go to v[] when V is true.
-// With a local reference, nring + nsl[1 - c^z] is the density plane of the source
-// plane z - c^z.
+// With a local reference, nring + nsl[1 - c^z] is the plane of density deviations
+// n - nbar of the source plane z - c^z.
 template <class ST, class CT, int TY, bool V>
 __device__ __forceinline__ P2<CT> staged_sum(const ST *stage, const float2 *nring, const int (&nsl)[3], int px,
-                                             int py, P2<CT> inv_scale, P2<CT> *v, P2<CT> nbar) {
+                                             int py, P2<CT> inv_scale, P2<CT> *v) {
   using G = StagedGeom<ST, TY>;
   using L = Lattice<kD3Q19>;
   const ST *base = stage + ((py + 1) * G::WX + px + G::OFF) * 2;
@@ -87,9 +87,9 @@ __device__ __forceinline__ P2<CT> staged_sum(const ST *stage, const float2 *nrin
   for (int i = 0; i < G::Q; ++i) {
     P2<CT> g = Codec2<ST, CT>::template load<true>(base + (i * G::RY * G::WX - L::c(i, 0)) * 2, inv_scale);
     if constexpr (G::LOCAL) {
-      // density of the source site (x - c_i, y - c_i^y, plane z - c_i^z)
+      // density deviation of the source site (x - c_i, y - c_i^y, plane z - c_i^z)
       const float2 ns = nring[nsl[1 - L::c(i, 2)] + (py - L::c(i, 1) + 2) * G::WXN + px + G::OFFN - L::c(i, 0)];
-      g = pfma(pbc(CT(L::w(i))), psub(pset(CT(ns.x), CT(ns.y)), nbar), g);
+      g = pfma(pbc(CT(L::w(i))), pset(CT(ns.x), CT(ns.y)), g);
     }
     if (V) v[i] = g;
     sum = padd(sum, g);
@@ -97,12 +97,12 @@ __device__ __forceinline__ P2<CT> staged_sum(const ST *stage, const float2 *nrin
   return sum;
 }
 
-// One block's column (bx, by) x z-chunk bz of the lattice described by a.
+// One block's column (bx, by), planes z0 .. zend - 1, of the lattice described by a.
 // NS: pipeline stages (2: the copy of plane k + 2 overlaps sum k and collide k - 1;
 // 1: the copy of plane k + 1 overlaps collide k - 1 only, for half the stage memory).
 // Window x coordinates wrap once: every chunk start lies in [-nx, 2 nx) for nx >= 32.
 template <class ST, class CT, int TY, int NS>
-__device__ __forceinline__ void staged_block(const StepArgs<CT> &a, int bx, int by, int bz,
+__device__ __forceinline__ void staged_block(const StepArgs<CT> &a, int bx, int by, int z0, int zend,
                                              unsigned char *smem_raw) {
   static_assert(NS == 1 || NS == 2, "one or two pipeline stages");
   using G = StagedGeom<ST, TY>;
@@ -123,8 +123,7 @@ __device__ __forceinline__ void staged_block(const StepArgs<CT> &a, int bx, int 
   const int64_t plane_elems = (int64_t)nx * ny;
   const ST *__restrict__ src = static_cast<const ST *>(a.src);
   ST *__restrict__ dst = static_cast<ST *>(a.dst);
-  const int x0 = bx * 32, y0 = by * TY, z0 = bz * a.tile_z;
-  const int zend = min(z0 + a.tile_z, nz);
+  const int x0 = bx * 32, y0 = by * TY;
   const int np = zend - z0 + 2;  // planes z0 - 1 .. zend
   const int own = (ty + 1) * G::SX + (tx + 1);
   const bool valid_xy = (x0 + tx < nx) && (y0 + ty < ny);
@@ -234,7 +233,7 @@ __device__ __forceinline__ void staged_block(const StepArgs<CT> &a, int bx, int 
     if (k + NS < np) rows_for(wrapz(z0 - 1 + k + NS));
     const int slot = k & (G::NPL - 1);
     {
-      const P2<CT> dn = staged_sum<ST, CT, TY, true>(stage, nring, nsl, tx, ty, a.inv_scale, mine, a.nbar);
+      const P2<CT> dn = staged_sum<ST, CT, TY, true>(stage, nring, nsl, tx, ty, a.inv_scale, mine);
       s_dn[slot * G::PLANE + own] = dn;
       if (a.self_on) s_psi[slot * G::PLANE + own] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp);
     }
@@ -242,7 +241,7 @@ __device__ __forceinline__ void staged_block(const StepArgs<CT> &a, int bx, int 
     for (int m = 0; m < NTASK; ++m) {
       if (task_on[m]) {
         const P2<CT> dn =
-            staged_sum<ST, CT, TY, false>(stage, nring, nsl, task_px[m], task_py[m], a.inv_scale, nullptr, a.nbar);
+            staged_sum<ST, CT, TY, false>(stage, nring, nsl, task_px[m], task_py[m], a.inv_scale, nullptr);
         s_dn[slot * G::PLANE + task_idx[m]] = dn;
         if (a.self_on) s_psi[slot * G::PLANE + task_idx[m]] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp);
       }
@@ -271,7 +270,31 @@ __device__ __forceinline__ void staged_block(const StepArgs<CT> &a, int bx, int 
 template <class ST, class CT, int TY, int NS, int MINB>
 __global__ void __launch_bounds__(32 * TY, MINB) sc_step_staged(const StepArgs<CT> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  staged_block<ST, CT, TY, NS>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+  int bx, by, z0, zend;
+  if (a.zbal_k > 0) {
+    // balanced split (1-D grid of K C + R blocks over C columns): chunk j of column c,
+    // columns c < R cut into K + 1 equal z-chunks, the others into K; chunk-major order
+    const int b = blockIdx.x, C = a.zbal_cols, K = a.zbal_k;
+    int j, c;
+    if (b < K * C) {
+      j = b / C;
+      c = b - j * C;
+    } else {
+      j = K;
+      c = b - K * C;
+    }
+    const int kc = K + (c < a.zbal_rem ? 1 : 0);
+    z0 = (int)((int64_t)j * a.nz / kc);
+    zend = (int)((int64_t)(j + 1) * a.nz / kc);
+    by = c / a.zbal_cols_x;
+    bx = c - by * a.zbal_cols_x;
+  } else {
+    bx = blockIdx.x;
+    by = blockIdx.y;
+    z0 = blockIdx.z * a.tile_z;
+    zend = min(z0 + a.tile_z, a.nz);
+  }
+  staged_block<ST, CT, TY, NS>(a, bx, by, z0, zend, smem_raw);
 }
 
 // Batched form (see sc_step_batched): block b works on items[b] = (lattice, bx,
@@ -297,7 +320,8 @@ __global__ void __launch_bounds__(32 * TY, MINB)
     s_a = a;
   }
   __syncthreads();
-  staged_block<ST, CT, TY, NS>(s_a, it.y, it.z, it.w, smem_raw);
+  const int z0 = it.w * s_a.tile_z;
+  staged_block<ST, CT, TY, NS>(s_a, it.y, it.z, z0, min(z0 + s_a.tile_z, s_a.nz), smem_raw);
 }
 
 }  // namespace scgb

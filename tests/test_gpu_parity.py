@@ -138,9 +138,10 @@ def test_staged_kernel_equals_generic_bitwise(B, storage):
     tile shape, pipeline depth and register budget."""
     st = getattr(B, f"SC_STORE_{storage}")
     outs = []
-    configs = [(1, 4, 5, 0, 0), (2, 4, 3, 2, 2), (2, 4, 3, 1, 3), (2, 4, 7, 2, 3), (2, 4, 1, 1, 2)]
+    # tile_z 0: the balanced z split (columns cut into K or K + 1 chunks, 1-D grid)
+    configs = [(1, 4, 5, 0, 0), (2, 4, 3, 2, 2), (2, 4, 3, 1, 3), (2, 4, 7, 2, 3), (2, 4, 1, 1, 2), (2, 4, 0, 2, 2)]
     if storage != "F64":
-        configs += [(2, 8, 7, 2, 1), (2, 8, 2, 1, 2), (2, 8, 13, 2, 2), (2, 8, 5, 1, 1)]
+        configs += [(2, 8, 7, 2, 1), (2, 8, 2, 1, 2), (2, 8, 13, 2, 2), (2, 8, 5, 1, 1), (2, 8, 0, 1, 2)]
     for variant, ty, tz, ns, mb in configs:
         sim2 = B.Simulation(B.make_params((96, 19, 13), psi_self=1, storage=st, tau=(1.0, 0.9), G=2.5,
                                           G_self=(-0.4, 0.1), tile_y=ty, tile_z=tz, variant=variant, stages=ns,
@@ -151,6 +152,31 @@ def test_staged_kernel_equals_generic_bitwise(B, storage):
         outs.append(sim2.state().cpu().numpy())
     for o in outs[1:]:
         np.testing.assert_array_equal(o, outs[0])
+
+
+@pytest.mark.parametrize("storage", ["F32", "F16"])
+def test_balanced_z_split_equals_generic(B, storage):
+    """A box whose balanced split gives columns of unequal chunk counts (on a
+    152-SM GPU with two resident blocks per SM: 304 blocks over 30 columns in
+    FP32, K = 10 with 4 columns of 11 chunks; over 15 columns in FP16, K = 20):
+    same state as the generic kernel, bit for bit."""
+    st = getattr(B, f"SC_STORE_{storage}")
+    shape = (96, 40, 128)
+    f = S.droplet(shape[::-1], (48, 20, 64), 12.0, n_in=0.85, n_out=0.15, amplitude=1e-3)
+    outs = []
+    for variant, tz in ((1, 32), (2, 0)):
+        sim = B.Simulation(B.make_params(shape, psi_self=1, storage=st, G=2.5, G_self=(-0.4, 0.0), tile_z=tz,
+                                         variant=variant), *f)
+        sim.step(5)
+        sim.sync()
+        if variant == 2:
+            cfg = sim.step_config
+            import torch
+
+            sms = torch.cuda.get_device_properties(0).multi_processor_count
+            assert cfg["variant"] == 2 and cfg["zsplit_k"] > 0 and cfg["blocks"] % sms == 0
+        outs.append(sim.state().cpu().numpy())
+    np.testing.assert_array_equal(outs[1], outs[0])
 
 
 @pytest.mark.parametrize("storage", ["F32", "F16", "BF16", "F64"])
