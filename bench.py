@@ -238,6 +238,21 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(ms: float, device) -> float:
+    """The slowest rank's time (ms): the whole job's time of a replica run."""
+    import torch
+    import torch.distributed as tdist
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(sites: int, steps_per_rank: int, world: int, ms: float) -> float:
+    """Site updates of all ranks (each rank a full replica) / the job's time."""
+    return sites * steps_per_rank * world / (ms * 1e-3) / 1e6
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
 
@@ -299,9 +314,7 @@ def run_gpu(args, rank, world, local_rank):
     B.sc_sync(sim.ctx)
     ms = start.elapsed_time(stop)
     if dist:
-        t = torch.tensor([ms], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dev)
     step_launches = sim.launches - launches0
     # per bench step: INNER fused steps + fields + profile partials + profile finalise + 2 bulk + sigma
     launches = step_launches + args.steps * 6
@@ -315,7 +328,7 @@ def run_gpu(args, rank, world, local_rank):
     peak, peak_kind = measured_peak()
     achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
 
-    value = sites * INNER * args.steps * world / (ms * 1e-3) / 1e6
+    value = whole_job_mlups(sites, INNER * args.steps, world, ms)
 
     # end to end through the host-buffer entry point: H2D of the initial fields, INNER steps, D2H of the densities
     e2e = None
@@ -331,7 +344,9 @@ def run_gpu(args, rank, world, local_rank):
             for _ in range(reps):
                 B.sc_run_host(params, hA, hB, INNER, oA, oB, ws, stream)
             e2e_s = (time.perf_counter() - t0) / reps
-        e2e = {"value": sites * INNER * world / e2e_s / 1e6, "unit": "MLUPS",
+        if world > 1:
+            e2e_s = max_over_ranks(e2e_s * 1e3, dev) * 1e-3
+        e2e = {"value": whole_job_mlups(sites, INNER, world, e2e_s * 1e3), "unit": "MLUPS",
                "h2d_bytes_per_step": 2 * sites * 8, "d2h_bytes_per_step": 2 * sites * 8,
                "note": f"sc_run_host per step: H2D of n_A0, n_B0 (FP64), create, {INNER} steps, D2H of n_A, n_B"}
 
@@ -449,6 +464,83 @@ def alt_throughput(B, storage, args, dev, stream):
             "hbm_frac": sites * BYTES_PER_SITE[storage] / (ms / INNER * 1e-3) / 1e9 / measured_peak()[0]}
 
 
+STUDY_RADII = (8, 10, 12, 16, 20, 24, 32, 40)
+
+
+def precision_study(args, dev):
+    """Errors of every result against the FP64-storage GPU path (itself within 1e-13 per step of the FP64
+    oracle): (1) the Tolman sweep -- 8 radii x (A-rich, B-rich) droplets in cubes of side 4 ceil(R) as one
+    batch, a 64x64x256 slab for sigma_0, Eq. sigma_c fitted on the device -- for the asymmetric (G_AA c_s^2 =
+    -0.2) and the symmetric coupling set; (2) the large droplet (side --study-size, R = side * 3/16,
+    asymmetric): dP, R_s, sigma_s, densities and velocity."""
+    import torch
+
+    import sc_synth
+    from paper_2112_02574_gb300 import binding as B
+    from paper_2112_02574_gb300 import tolman
+
+    codes = {"f64": B.SC_STORE_F64, "f32": B.SC_STORE_F32, "f16": B.SC_STORE_F16, "bf16": B.SC_STORE_BF16}
+    T = args.study_steps
+    mk = lambda shape, centre, R, a_rich: sc_synth.droplet(shape, centre, R, n_in=0.95, n_out=0.05, amplitude=1e-3,
+                                                           a_rich=a_rich)
+    slab = lambda shape: sc_synth.slab(shape, shape[0] / 2, amplitude=1e-3)
+    out = {"study": "precision of every result vs the FP64-storage path; Tolman length from Eq. sigma_c",
+           "tolman_steps": T, "radii": list(STUDY_RADII), "sides": [tolman.droplet_side(R) for R in STUDY_RADII]}
+    for name, gs in (("asymmetric", (-0.6, 0.0)), ("symmetric", (0.0, 0.0))):
+        per = {}
+        for st in ("f64", "f32", "f16", "bf16"):
+            t0 = time.perf_counter()
+            kw = dict(lattice=B.SC_D3Q19, psi_self=B.SC_PSI_EXP, storage=codes[st], G=G_CROSS, G_self=gs)
+            drops = tolman.droplet_sweep(STUDY_RADII, (1, -1), mk, kw, T, device=dev)
+            s0 = tolman.flat_sigma0((64, 64, 256), slab, kw, T, device=dev)
+            per[st] = {"droplets": drops, "sigma0_flat": float(s0.item()), "fit_fixed_sigma0": tolman.fit(drops, s0),
+                       "fit_free_sigma0": tolman.fit(drops, None), "seconds": time.perf_counter() - t0}
+            torch.cuda.empty_cache()
+        ref = per["f64"]
+        for st in ("f32", "f16", "bf16"):
+            got = per[st]
+            rel = lambda k: max(abs(a[k] - b[k]) / abs(b[k]) for a, b in zip(got["droplets"], ref["droplets"]))
+            got["errors_vs_f64"] = {
+                "dP_max_rel": rel("dP"), "R_s_max_rel": rel("R_s"), "sigma_s_max_rel": rel("sigma_s"),
+                "sigma0_rel": abs(got["sigma0_flat"] - ref["sigma0_flat"]) / abs(ref["sigma0_flat"]),
+                "delta_abs": abs(got["fit_fixed_sigma0"]["delta"] - ref["fit_fixed_sigma0"]["delta"]),
+                "rigidity_abs": abs(got["fit_fixed_sigma0"]["rigidity"] - ref["fit_fixed_sigma0"]["rigidity"])}
+        out[name] = per
+    # the large droplet
+    n = args.study_size
+    shape = (n, n, n)
+    R = n * 3.0 / 16.0
+    nA0, nB0 = sc_synth.droplet(shape, (n // 2,) * 3, R, n_in=0.95, n_out=0.05, amplitude=1e-3)
+    big = {"shape": list(shape), "R": R, "steps": args.study_size_steps}
+    refm = None
+    for st in ("f64", "f32", "f16", "bf16"):
+        t0 = time.perf_counter()
+        p = B.make_params(shape, lattice=B.SC_D3Q19, psi_self=B.SC_PSI_EXP, storage=codes[st], G=G_CROSS,
+                          G_self=(-0.6, 0.0))
+        sim = B.Simulation(p, nA0, nB0, device=dev)
+        sim.step(args.study_size_steps)
+        _, o = B.surface_of_tension(sim, (n // 2,) * 3, 0.5)
+        nA, nB, u = sim.moments()
+        sim.sync()
+        o = o.cpu().numpy()
+        res = {"dP": float(o[0]), "R_s": float(o[2]), "sigma_s": float(o[3]), "seconds": time.perf_counter() - t0}
+        if refm is None:
+            refm = (nA, nB, u, res)
+        else:
+            rA, rB, ru, rres = refm
+            res["errors_vs_f64"] = {
+                **{k + "_rel": abs(res[k] - rres[k]) / abs(rres[k]) for k in ("dP", "R_s", "sigma_s")},
+                "n_max_rel": max(float((nA - rA).abs().max() / rA.abs().max()),
+                                 float((nB - rB).abs().max() / rB.abs().max())),
+                "u_max_abs": float((u - ru).abs().max()), "u_max": float(ru.abs().max())}
+            del nA, nB, u
+        big[st] = res
+        del sim
+        torch.cuda.empty_cache()
+    out["large_droplet"] = big
+    print(json.dumps(out), flush=True)
+
+
 def main():
     global INNER
     ap = argparse.ArgumentParser()
@@ -469,6 +561,11 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched radius sweep block")
     ap.add_argument("--inner", type=int, default=INNER, help="time steps per benchmark step (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--study", action="store_true",
+                    help="run only the precision / Tolman-length study (minutes) and print its JSON line")
+    ap.add_argument("--study-steps", type=int, default=16384, help="time steps of the Tolman sweep and slab")
+    ap.add_argument("--study-size", type=int, default=512, help="side of the large droplet of the study")
+    ap.add_argument("--study-size-steps", type=int, default=4096, help="time steps of the large droplet")
     args = ap.parse_args()
     INNER = args.inner
     rank = int(os.environ.get("RANK", "0"))
@@ -476,6 +573,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.study:
+        if rank == 0:
+            precision_study(args, "cuda")
         return
     if world > 1:
         import torch

@@ -165,6 +165,25 @@ sc_status sc_bulk_pressure_at(sc_ctx *ctx, const int32_t node[3], double *out);
 sc_status sc_sigma_minimum(const double *rows, int32_t nbins, const double *P_in_out, int32_t dim, double R_lo,
                            double R_hi, double R_step, double *out, void *stream);
 
+/* Flat-interface surface tension (section 4, the sigma_0 of Eq. sigma_c):
+ * sigma_0 = sum over the planes z >= nbins / 2 of P_N(z) - P_T(z), from the rows
+ * of a PLANAR_Z profile (one bin per plane) of a periodic slab whose second
+ * interface lies in the upper half.  rows: device FP64 [nbins][6]; out: device
+ * FP64 [1].  Deterministic; asynchronous on stream. */
+sc_status sc_sigma0_flat(const double *rows, int32_t nbins, double *out, void *stream);
+
+/* Curvature expansion of the surface tension (Eq. sigma_c, section 1; the
+ * Tolman length delta and the rigidity combination 2 kbar + k): least squares
+ * of sigma_s = sigma_0 (1 - 2 delta / R_s + (2 kbar + k) / R_s^2) over n droplets,
+ * in FP64 on the device.  Rs, sigma_s: device FP64 [n], R_s signed (negative for
+ * droplets of the other component, section 4); order 1 or 2 (1: no 1/R_s^2
+ * term); sigma0: device FP64 [1] holding a fixed sigma_0 (e.g. from
+ * sc_sigma0_flat), or NULL to fit it.  out: device FP64 [4] = (sigma_0, delta,
+ * 2 kbar + k (NaN for order 1), rms residual of sigma_s).  Needs n >= number of
+ * unknowns (order, plus one when sigma_0 is fitted).  Asynchronous on stream. */
+sc_status sc_curvature_fit(const double *Rs, const double *sigma_s, int32_t n, int32_t order, const double *sigma0,
+                           double *out, void *stream);
+
 /* Pressure-tensor profile without any device allocation.  The paper has no
  * counterpart to this entry point; it exists for callers that cannot allocate
  * device memory at the point of the call -- for instance code that has handed

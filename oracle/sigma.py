@@ -106,13 +106,23 @@ def sigma0_flat(PN, PT) -> float:
     return float(np.sum(PN[L // 2:] - PT[L // 2:]))
 
 
-def curvature_fit(Rs, sigma_s, order: int = 2) -> dict:
+def curvature_fit(Rs, sigma_s, order: int = 2, sigma0=None) -> dict:
     """Least-squares fit of Eq. sigma_c, sigma(R_s) = sigma_0 (1 - 2 delta/R_s + (2kbar + k)/R_s^2),
-    as a polynomial in 1/R_s (negative R_s for droplets of the other component)."""
+    as a polynomial in 1/R_s (negative R_s for droplets of the other component).  With sigma0
+    given (the flat-interface value) only delta and 2kbar + k are fitted, to sigma_s/sigma_0 - 1."""
     x = 1.0 / np.asarray(Rs, dtype=np.float64)
-    c = np.polynomial.polynomial.polyfit(x, np.asarray(sigma_s, dtype=np.float64), order)
-    s0 = c[0]
-    out = {"sigma0": float(s0), "delta": float(-c[1] / (2.0 * s0))}
+    y = np.asarray(sigma_s, dtype=np.float64)
+    if sigma0 is None:
+        c = np.polynomial.polynomial.polyfit(x, y, order)
+        s0 = c[0]
+        out = {"sigma0": float(s0), "delta": float(-c[1] / (2.0 * s0))}
+        if order >= 2:
+            out["rigidity"] = float(c[2] / s0)
+        return out
+    s0 = float(sigma0)
+    A = np.stack([x ** p for p in range(1, order + 1)], axis=1)
+    b, *_ = np.linalg.lstsq(A, y / s0 - 1.0, rcond=None)
+    out = {"sigma0": s0, "delta": float(-b[0] / 2.0)}
     if order >= 2:
-        out["rigidity"] = float(c[2] / s0)
+        out["rigidity"] = float(b[1])
     return out

@@ -72,6 +72,8 @@ def _load():
         "sc_pressure_profile": (I32, [V, I32, ctypes.POINTER(D), D, I32, V]),
         "sc_bulk_pressure_at": (I32, [V, ctypes.POINTER(I32), V]),
         "sc_sigma_minimum": (I32, [V, I32, V, I32, D, D, D, V, V]),
+        "sc_sigma0_flat": (I32, [V, I32, V, V]),
+        "sc_curvature_fit": (I32, [V, V, I32, I32, V, V, V]),
         "sc_pressure_profile_noalloc": (I32, [P, V, V, I32, ctypes.POINTER(D), D, I32, V, V]),
         "sc_totals": (I32, [V, V]),
         "sc_sync": (I32, [V]),
@@ -184,6 +186,15 @@ def sc_bulk_pressure_at(ctx, node, out):
 def sc_sigma_minimum(rows, P_in_out, dim, R_lo, R_hi, R_step, out, stream=None):
     _check(lib.sc_sigma_minimum(_ptr(rows), rows.shape[0], _ptr(P_in_out), int(dim), float(R_lo), float(R_hi),
                                 float(R_step), _ptr(out), _stream_ptr(stream)))
+
+
+def sc_sigma0_flat(rows, out, stream=None):
+    _check(lib.sc_sigma0_flat(_ptr(rows), rows.shape[0], _ptr(out), _stream_ptr(stream)))
+
+
+def sc_curvature_fit(Rs, sigma_s, order, sigma0, out, stream=None):
+    _check(lib.sc_curvature_fit(_ptr(Rs), _ptr(sigma_s), int(Rs.numel()), int(order),
+                                _ptr(sigma0) if sigma0 is not None else None, _ptr(out), _stream_ptr(stream)))
 
 
 def sc_totals(ctx, out):
@@ -431,3 +442,22 @@ def surface_of_tension(sim: Simulation, centre, bin_width=0.5, nbins=None, in_no
     r_max = nbins * (bin_width if kind == SC_PROFILE_RADIAL else 1.0)
     sc_sigma_minimum(rows, pio, dim, R_step, r_max, R_step, out, sim.stream)
     return rows, out
+
+
+def sigma0_flat(sim: Simulation):
+    """sigma_0 of a periodic slab along z (section 4): planar profile, then
+    sc_sigma0_flat, on the device.  Returns (rows, sigma_0 as a CUDA tensor [1])."""
+    rows = sim.profile(SC_PROFILE_PLANAR_Z, (0.0, 0.0, 0.0), 1.0, sim.shape[2])
+    out = torch.empty(1, dtype=torch.float64, device=sim.device)
+    sc_sigma0_flat(rows, out, sim.stream)
+    return rows, out
+
+
+def curvature_fit(Rs, sigma_s, order=2, sigma0=None, stream=None):
+    """Eq. sigma_c fit over droplets on the device: Rs, sigma_s CUDA float64
+    tensors (R_s negative for droplets of the other component), sigma0 a CUDA
+    float64 [1] tensor or None (fitted).  Returns out[4] = (sigma_0, delta,
+    2kbar + k, rms residual)."""
+    out = torch.empty(4, dtype=torch.float64, device=Rs.device)
+    sc_curvature_fit(Rs.contiguous(), sigma_s.contiguous(), order, sigma0, out, stream)
+    return out

@@ -652,6 +652,25 @@ sc_status sc_sigma_minimum(const double *rows, int32_t nbins, const double *P_in
   return SC_OK;
 }
 
+sc_status sc_sigma0_flat(const double *rows, int32_t nbins, double *out, void *stream) {
+  if (!rows || !out) return fail(SC_EINVAL, "rows and out must be non-NULL");
+  if (nbins < 2) return fail(SC_EINVAL, "need at least two planes");
+  sigma0_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(rows, nbins, out);
+  SC_CUDA(cudaGetLastError());
+  return SC_OK;
+}
+
+sc_status sc_curvature_fit(const double *Rs, const double *sigma_s, int32_t n, int32_t order, const double *sigma0,
+                           double *out, void *stream) {
+  if (!Rs || !sigma_s || !out) return fail(SC_EINVAL, "Rs, sigma_s and out must be non-NULL");
+  if (order != 1 && order != 2) return fail(SC_EINVAL, "order must be 1 or 2");
+  const int unknowns = order + (sigma0 ? 0 : 1);
+  if (n < unknowns || n > (1 << 20)) return fail(SC_EINVAL, "need %d to 2^20 droplets, got %d", unknowns, n);
+  curvature_fit_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(Rs, sigma_s, n, order, sigma0, out);
+  SC_CUDA(cudaGetLastError());
+  return SC_OK;
+}
+
 sc_status sc_totals(sc_ctx *c, double *out) {
   if (!c || !out) return fail(SC_EINVAL, "ctx and out must be non-NULL");
   const int blocks = grid_for(c->N, 256) < kMaxPartialBlocks ? grid_for(c->N, 256) : kMaxPartialBlocks;

@@ -439,6 +439,89 @@ __global__ void __launch_bounds__(32) sigma_kernel(const double *rows, int nbins
   }
 }
 
+// Flat-interface tension (section 4): sigma_0 = sum over the planes z >= nbins / 2 of
+// P_N(z) - P_T(z) from planar profile rows; one warp, lane-strided sums and a fixed
+// shuffle tree (deterministic).
+__global__ void __launch_bounds__(32) sigma0_kernel(const double *rows, int nbins, double *out) {
+  const int lane = threadIdx.x;
+  double acc = 0.0;
+  for (int z = nbins / 2 + lane; z < nbins; z += 32) acc += rows[z * 6 + 1] - rows[z * 6 + 2];
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (lane == 0) out[0] = acc;
+}
+
+// Curvature expansion of the surface tension (Eq. sigma_c),
+// sigma_s = sigma_0 (1 - 2 delta x + c x^2), x = 1 / R_s, by least squares over n
+// droplets: sigma_0 fitted (columns 1, x, x^2) or held at *sigma0 (columns x, x^2 on
+// sigma_s / sigma_0 - 1); order 1 drops the x^2 column.  The normal equations are
+// formed in x scaled by 1 / max|x| and solved by Gaussian elimination with partial
+// pivoting; one thread, fixed order.  out = (sigma_0, delta, c (NaN for order 1), rms
+// residual of sigma_s).
+__global__ void curvature_fit_kernel(const double *Rs, const double *sig, int n, int order, const double *sigma0,
+                                     double *out) {
+  if (threadIdx.x != 0) return;
+  const bool fixed = sigma0 != nullptr;
+  const double s0f = fixed ? sigma0[0] : 0.0;
+  double xm = 0.0;
+  for (int i = 0; i < n; ++i) xm = fmax(xm, fabs(1.0 / Rs[i]));
+  const double sc = xm > 0.0 ? 1.0 / xm : 1.0;
+  const int m = fixed ? order : order + 1;
+  double G[3][4];
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 4; ++l) G[k][l] = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double t = sc / Rs[i];
+    const double col[3] = {fixed ? t : 1.0, fixed ? t * t : t, t * t};
+    const double y = fixed ? sig[i] / s0f - 1.0 : sig[i];
+    for (int k = 0; k < m; ++k) {
+      for (int l = 0; l < m; ++l) G[k][l] += col[k] * col[l];
+      G[k][3] += col[k] * y;
+    }
+  }
+  // elimination on the augmented m x (m + 1) system
+  for (int k = 0; k < m; ++k) {
+    int piv = k;
+    for (int r = k + 1; r < m; ++r)
+      if (fabs(G[r][k]) > fabs(G[piv][k])) piv = r;
+    if (piv != k)
+      for (int l = 0; l < 4; ++l) {
+        const double t = G[k][l];
+        G[k][l] = G[piv][l];
+        G[piv][l] = t;
+      }
+    for (int r = k + 1; r < m; ++r) {
+      const double f = G[r][k] / G[k][k];
+      for (int l = k; l < 4; ++l) G[r][l] -= f * G[k][l];
+    }
+  }
+  double c[3] = {0.0, 0.0, 0.0};
+  for (int k = m - 1; k >= 0; --k) {
+    double v = G[k][3];
+    for (int l = k + 1; l < m; ++l) v -= G[k][l] * c[l];
+    c[k] = v / G[k][k];
+  }
+  double s0, a1, a2;  // sigma_s = s0 + a1 x + a2 x^2 in unscaled x
+  if (fixed) {
+    s0 = s0f;
+    a1 = s0f * c[0] * sc;
+    a2 = order == 2 ? s0f * c[1] * sc * sc : 0.0;
+  } else {
+    s0 = c[0];
+    a1 = c[1] * sc;
+    a2 = order == 2 ? c[2] * sc * sc : 0.0;
+  }
+  double rss = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double x = 1.0 / Rs[i];
+    const double d = s0 + a1 * x + a2 * x * x - sig[i];
+    rss += d * d;
+  }
+  out[0] = s0;
+  out[1] = -a1 / (2.0 * s0);
+  out[2] = order == 2 ? a2 / s0 : NAN;
+  out[3] = sqrt(rss / n);
+}
+
 // Deterministic FP64 totals: per-block partial sums (fixed grid-stride order,
 // fixed tree) of mass_A, mass_B and momentum; finalised in block order.
 template <int LAT, class ST>

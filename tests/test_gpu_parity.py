@@ -337,6 +337,56 @@ def test_sigma_minimum_matches_oracle(B):
         assert o[5] == pytest.approx(sg, rel=1e-9)
 
 
+def test_sigma0_flat_matches_oracle(B):
+    """Section 4: sigma_0 of a slab, the device reduction of the device planar
+    profile against the oracle's sum over the oracle's profile (FP64 storage)."""
+    import oracle.sigma as SG
+
+    shape = (16, 12, 64)
+    nA0, nB0 = S.slab(shape[::-1], 32.0, amplitude=1e-3)
+    p = B.make_params(shape, psi_self=1, storage=B.SC_STORE_F64, G=3.6, G_self=(-0.6, 0.0))
+    sim = B.Simulation(p, nA0, nB0)
+    sim.step(40)
+    rows, s0 = B.sigma0_flat(sim)
+    op = oracle.Params(shape=shape, lattice=oracle.D3Q19, psi_self=oracle.PSI_EXP, G=3.6, G_self=(-0.6, 0.0))
+    f = oracle.step(op, oracle.init(op, nA0, nB0), 40)
+    oA, oB, _ = oracle.moments(op, f, with_u=False)
+    want_rows = oracle.profile(op, oA, oB, oracle.PLANAR_Z, (0.0, 0.0, 0.0), 1.0, shape[2])
+    want = SG.sigma0_flat(want_rows[:, 1], want_rows[:, 2])
+    assert abs(want) > 1e-3
+    assert s0.item() == pytest.approx(want, rel=1e-11)
+    g = rows.cpu().numpy()
+    assert s0.item() == pytest.approx(SG.sigma0_flat(g[:, 1], g[:, 2]), rel=1e-13)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("fixed", [False, True])
+def test_curvature_fit_matches_oracle(B, order, fixed):
+    """Eq. sigma_c fit on the device against the oracle's least squares, on noisy
+    synthetic (R_s, sigma_s) of A-rich (+R_s) and B-rich (-R_s) droplets."""
+    import torch
+
+    import oracle.sigma as SG
+
+    rng = np.random.default_rng(11)
+    Rs = np.concatenate([np.linspace(6.0, 40.0, 9), -np.linspace(7.0, 38.0, 7)])
+    s0, delta, rig = 0.0712, 0.41, 1.3
+    sig = s0 * (1 - 2 * delta / Rs + rig / Rs**2) * (1 + 1e-4 * rng.standard_normal(Rs.size))
+    dev = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
+    sig0 = dev([s0 * 1.001]) if fixed else None
+    out = B.curvature_fit(dev(Rs), dev(sig), order=order, sigma0=sig0).cpu().numpy()
+    want = SG.curvature_fit(Rs, sig, order=order, sigma0=s0 * 1.001 if fixed else None)
+    assert out[0] == pytest.approx(want["sigma0"], rel=1e-10)
+    assert out[1] == pytest.approx(want["delta"], rel=1e-8)
+    if order == 2:
+        assert out[2] == pytest.approx(want["rigidity"], rel=1e-7)
+    else:
+        assert np.isnan(out[2])
+    x = 1.0 / Rs
+    model = want["sigma0"] * (1 - 2 * want["delta"] * x + (want.get("rigidity", 0.0)) * x**2)
+    assert out[3] == pytest.approx(np.sqrt(np.mean((model - sig) ** 2)), rel=1e-6)
+
+
 def test_run_host_matches_device_path(B):
     import torch
 

@@ -157,3 +157,21 @@ def test_curvature_fit_recovers_coefficients():
     assert fit["sigma0"] == pytest.approx(s0, rel=1e-10)
     assert fit["delta"] == pytest.approx(delta, rel=1e-9)
     assert fit["rigidity"] == pytest.approx(rig, rel=1e-8)
+
+
+def test_curvature_fit_with_fixed_sigma0():
+    """Eq. sigma_c with sigma_0 held at the flat-interface value: exact data give
+    back delta and 2kbar + k; a wrong sigma_0 shows up as a non-zero residual
+    (the fit cannot absorb a constant offset)."""
+    s0, delta, rig = 0.104, -0.21, 0.8
+    Rs = np.array([5.0, 7.0, 10.0, 14.0, 20.0, 40.0, -5.0, -8.0, -13.0, -25.0])
+    sig = s0 * (1 - 2 * delta / Rs + rig / Rs**2)
+    fit = SG.curvature_fit(Rs, sig, sigma0=s0)
+    assert fit["delta"] == pytest.approx(delta, rel=1e-10)
+    assert fit["rigidity"] == pytest.approx(rig, rel=1e-9)
+    lin = SG.curvature_fit(Rs, s0 * (1 - 2 * delta / Rs), order=1, sigma0=s0)
+    assert lin["delta"] == pytest.approx(delta, rel=1e-12) and "rigidity" not in lin
+    bad = SG.curvature_fit(Rs, sig, sigma0=1.05 * s0)
+    x = 1.0 / Rs
+    model = 1.05 * s0 * (1 - 2 * bad["delta"] * x + bad["rigidity"] * x**2)
+    assert np.sqrt(np.mean((model - sig) ** 2)) > 1e-4
