@@ -14,6 +14,7 @@ on the same workload (a bounded sample per step) on the host cores.
 from __future__ import annotations
 
 import argparse
+import math
 import json
 import os
 import statistics
@@ -541,6 +542,60 @@ def precision_study(args, dev):
     print(json.dumps(out), flush=True)
 
 
+PAPER_SIDES = (25, 31, 37, 41, 51, 57, 65)  # section 4's system sizes up to 65; R = L / 4
+PAPER_DGAB = (0.0, 0.48, -0.48, 0.88, -0.88)
+
+
+def paper_couplings(dGAB: float, dGc: float = 0.4):
+    """Eq. self_p: G_AA = G_c [1 - dG_c (1 + dG_AB)], G_BB = G_c (1 - dG_c), with G_c c_s^2 = -e^2 / 3
+    (the critical self coupling of psi = exp(-1/n), printed as -2.463) and G c_s^2 = 0.5 (section 4)."""
+    Gc = -math.e ** 2
+    return dict(G=1.5, G_self=(Gc * (1.0 - dGc * (1.0 + dGAB)), Gc * (1.0 - dGc)))
+
+
+def paper_tolman_study(args, dev):
+    """The Tolman sweep on the paper's couplings (section 4): per dG_AB a flat-interface pre-run (slab
+    16 x 16 x 128) gives the bulk densities and sigma_0; A-rich and B-rich droplets of side L (odd, the
+    paper's sizes) and R = L / 4 start from those densities; all droplets of all dG_AB run as one batch;
+    Eq. sigma_c is fitted on the device with sigma_0 held at the slab value."""
+    import sc_synth
+    from paper_2112_02574_gb300 import binding as B
+    from paper_2112_02574_gb300 import tolman
+
+    code = {"f64": B.SC_STORE_F64, "f32": B.SC_STORE_F32, "f16": B.SC_STORE_F16, "bf16": B.SC_STORE_BF16}[
+        args.study_storage]
+    T = args.study_steps
+    ntot = args.study_density
+    out = {"study": "Tolman length on the couplings of Eq. self_p (dG_c = 0.4, G c_s^2 = 0.5, psi = exp(-1/n))",
+           "steps": T, "storage": args.study_storage, "total_density": ntot, "sides": list(PAPER_SIDES), "sets": {}}
+    members, flats = [], {}
+    for d in PAPER_DGAB:
+        kw = dict(lattice=B.SC_D3Q19, psi_self=B.SC_PSI_EXP, storage=code, **paper_couplings(d))
+        slab = lambda shape: sc_synth.slab(shape, shape[0] / 2, n_rich=0.95 * ntot, n_poor=0.05 * ntot,
+                                           amplitude=1e-3)
+        fl = tolman.flat_densities((16, 16, 128), slab, kw, T, device=dev)
+        flats[d] = fl
+        for L in PAPER_SIDES:
+            for sign in (1, -1):
+                inside = (fl["A_in"], fl["B_in"]) if sign > 0 else (fl["A_out"], fl["B_out"])
+                outside = (fl["A_out"], fl["B_out"]) if sign > 0 else (fl["A_in"], fl["B_in"])
+                f = sc_synth.droplet_ab((L, L, L), (L // 2,) * 3, L / 4.0, inside[0], outside[0], inside[1],
+                                        outside[1], amplitude=1e-3)
+                members.append({"L": L, "R": L / 4.0, "sign": sign, "params": kw, "fields": f, "tag": d})
+    t0 = time.perf_counter()
+    drops = tolman.sweep(members, T, device=dev)
+    out["sweep_seconds"] = time.perf_counter() - t0
+    import torch
+
+    for d in PAPER_DGAB:
+        ds = [x for x in drops if x["tag"] == d]
+        s0 = torch.tensor([flats[d]["sigma0"]], dtype=torch.float64, device=dev)
+        out["sets"][f"{d:+.2f}"] = {"flat": flats[d], "fit_fixed_sigma0": tolman.fit(ds, s0, device=dev),
+                                    "fit_free_sigma0": tolman.fit(ds, None, device=dev),
+                                    "max_dP_change": max(x["dP_change"] for x in ds), "droplets": ds}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     global INNER
     ap = argparse.ArgumentParser()
@@ -561,8 +616,11 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched radius sweep block")
     ap.add_argument("--inner", type=int, default=INNER, help="time steps per benchmark step (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--study", action="store_true",
-                    help="run only the precision / Tolman-length study (minutes) and print its JSON line")
+    ap.add_argument("--study", choices=["precision", "paper"],
+                    help="run only a study (minutes) and print its JSON line: precision = every result in each "
+                         "storage against the FP64 path; paper = Tolman length on the couplings of Eq. self_p")
+    ap.add_argument("--study-storage", default="f32", choices=["f64", "f32", "f16", "bf16"])
+    ap.add_argument("--study-density", type=float, default=1.0, help="total density of the paper study")
     ap.add_argument("--study-steps", type=int, default=16384, help="time steps of the Tolman sweep and slab")
     ap.add_argument("--study-size", type=int, default=512, help="side of the large droplet of the study")
     ap.add_argument("--study-size-steps", type=int, default=4096, help="time steps of the large droplet")
@@ -576,7 +634,7 @@ def main():
         return
     if args.study:
         if rank == 0:
-            precision_study(args, "cuda")
+            (precision_study if args.study == "precision" else paper_tolman_study)(args, "cuda")
         return
     if world > 1:
         import torch

@@ -62,7 +62,7 @@ bool staged_eligible(const sc_params *p, int tile_y) {
   if (p->lattice != SC_D3Q19 || p->stencil != SC_FORCE_E4 || p->nx < 32 || p->nx % chunk_sites(p->storage) != 0)
     return false;
   if (p->storage == SC_STORE_F64) return tile_y == 4;
-  return tile_y == 4 || tile_y == 8;
+  return tile_y == 4 || tile_y == 8 || tile_y == 16;
 }
 
 // Kernel choice and tiles (measured sweeps at 128^3, 256^3 and 512^3 set the defaults).
@@ -77,10 +77,10 @@ int default_tile_y(const sc_params *p) {
   if (use_staged(p)) return staged_default_tile_y(p);
   return p->lattice == SC_D3Q19 ? 8 : 4;
 }
-int effective_stages(const sc_params *p, int tile_y) { return p->stages ? p->stages : (tile_y == 8 ? 1 : 2); }
+int effective_stages(const sc_params *p, int tile_y) { return p->stages ? p->stages : (tile_y == 4 ? 2 : 1); }
 int effective_blocks_per_sm(const sc_params *p, int tile_y) {
   if (p->blocks_per_sm) return p->blocks_per_sm;
-  return tile_y == 8 ? 2 : (is_16bit(p->storage) ? 3 : 2);
+  return tile_y == 16 ? 1 : (tile_y == 8 ? 2 : (is_16bit(p->storage) ? 3 : 2));
 }
 int default_tile_z(const sc_params *p) {
   if (p->lattice == SC_D2Q9) return 1;
@@ -99,19 +99,23 @@ sc_status validate(const sc_params *p) {
   if (p->stencil == SC_FORCE_E6 && p->lattice != SC_D3Q19) return fail(SC_EINVAL, "the E6 stencil needs D3Q19");
   if (p->psi_self != SC_PSI_N && p->psi_self != SC_PSI_EXP) return fail(SC_EINVAL, "unknown psi %d", p->psi_self);
   if (store_bytes(p->storage) == 0) return fail(SC_EINVAL, "unknown storage %d", p->storage);
-  if (p->tile_y != 0 && p->tile_y != 1 && p->tile_y != 2 && p->tile_y != 4 && p->tile_y != 8)
-    return fail(SC_EINVAL, "tile_y must be 0, 1, 2, 4 or 8");
+  if (p->tile_y != 0 && p->tile_y != 1 && p->tile_y != 2 && p->tile_y != 4 && p->tile_y != 8 && p->tile_y != 16)
+    return fail(SC_EINVAL, "tile_y must be 0, 1, 2, 4, 8 or 16");
   if (p->tile_z < 0) return fail(SC_EINVAL, "tile_z must be >= 0");
   if (p->variant < 0 || p->variant > 2) return fail(SC_EINVAL, "variant must be 0, 1 or 2");
   if (p->stages < 0 || p->stages > 2) return fail(SC_EINVAL, "stages must be 0, 1 or 2");
   if (p->blocks_per_sm < 0 || p->blocks_per_sm > 3) return fail(SC_EINVAL, "blocks_per_sm must be 0 .. 3");
   if (p->variant == 2 && !staged_eligible(p, p->tile_y ? p->tile_y : staged_default_tile_y(p)))
     return fail(SC_EINVAL, "the staged step kernel needs D3Q19, E4, nx >= 32, nx a multiple of %d for this "
-                           "storage and tile_y 4 or 8 (4 for F64 storage)", chunk_sites(p->storage));
-  if (use_staged(p) && p->blocks_per_sm) {
-    const int ty = default_tile_y(p), lo = ty == 8 ? 1 : 2, hi = ty == 8 ? 2 : 3;
-    if (p->blocks_per_sm < lo || p->blocks_per_sm > hi)
+                           "storage and tile_y 4, 8 or 16 (4 for F64 storage)", chunk_sites(p->storage));
+  if (p->tile_y == 16 && !use_staged(p)) return fail(SC_EINVAL, "tile_y 16 needs the staged kernel");
+  if (use_staged(p)) {
+    const int ty = default_tile_y(p);
+    const int lo = ty == 4 ? 2 : 1, hi = ty == 4 ? 3 : (ty == 8 ? 2 : 1);
+    if (p->blocks_per_sm && (p->blocks_per_sm < lo || p->blocks_per_sm > hi))
       return fail(SC_EINVAL, "blocks_per_sm must be 0 or %d .. %d for the staged kernel with tile_y %d", lo, hi, ty);
+    if (ty == 16 && effective_stages(p, ty) == 2 && !is_16bit(p->storage))
+      return fail(SC_EINVAL, "two stages of 32 x 16 tiles exceed shared memory in this storage");
   }
   for (int J = 0; J < 2; ++J)
     if (!(p->tau[J] > 0.5) || !isfinite(p->tau[J])) return fail(SC_EINVAL, "tau[%d] must be > 1/2", J);

@@ -48,48 +48,59 @@ cudaError_t staged_occupancy_one(int *blocks) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, 32 * TY, smem);
 }
 
-// Instantiated staged configurations (tile_y, stages, blocks per SM):
-// (4, 1|2, 2|3) and, except for F64 storage, (8, 1|2, 1|2).
-// Resident blocks per SM of the staged kernel for (tile_y, stages, blocks_per_sm).
-template <class ST, class CT>
-cudaError_t staged_occupancy(int ty, int ns, int mb, int *blocks) {
+// One instantiated staged configuration, as a tag type.
+template <int TY_, int NS_, int MINB_>
+struct StagedCfg {
+  static constexpr int TY = TY_, NS = NS_, MINB = MINB_;
+};
+
+// Calls fn(StagedCfg<...>{}) for the instantiated configuration (tile_y, stages,
+// blocks per SM) that serves the request, or returns fallback.  Instantiated:
+// (4, 1|2, 2|3) for every storage; (8, 1|2, 1|2) and (16, 1, 1) except F64;
+// (16, 2, 1) for 16-bit storage only (two 32 x 16 FP32 stages do not fit).
+// blocks_per_sm below the smallest instantiated value takes that value.
+template <class ST, class Fn, class R>
+R with_staged_cfg(int ty, int ns, int mb, R fallback, Fn &&fn) {
   if (ty == 4) {
-    if (ns == 2 && mb <= 2) return staged_occupancy_one<ST, CT, 4, 2, 2>(blocks);
-    if (ns == 2 && mb == 3) return staged_occupancy_one<ST, CT, 4, 2, 3>(blocks);
-    if (ns == 1 && mb <= 2) return staged_occupancy_one<ST, CT, 4, 1, 2>(blocks);
-    if (ns == 1 && mb == 3) return staged_occupancy_one<ST, CT, 4, 1, 3>(blocks);
+    if (ns == 2 && mb <= 2) return fn(StagedCfg<4, 2, 2>{});
+    if (ns == 2 && mb == 3) return fn(StagedCfg<4, 2, 3>{});
+    if (ns == 1 && mb <= 2) return fn(StagedCfg<4, 1, 2>{});
+    if (ns == 1 && mb == 3) return fn(StagedCfg<4, 1, 3>{});
   }
   if constexpr (sizeof(ST) < 8) {
     if (ty == 8) {
-      if (ns == 2 && mb <= 1) return staged_occupancy_one<ST, CT, 8, 2, 1>(blocks);
-      if (ns == 2 && mb == 2) return staged_occupancy_one<ST, CT, 8, 2, 2>(blocks);
-      if (ns == 1 && mb <= 1) return staged_occupancy_one<ST, CT, 8, 1, 1>(blocks);
-      if (ns == 1 && mb == 2) return staged_occupancy_one<ST, CT, 8, 1, 2>(blocks);
+      if (ns == 2 && mb <= 1) return fn(StagedCfg<8, 2, 1>{});
+      if (ns == 2 && mb == 2) return fn(StagedCfg<8, 2, 2>{});
+      if (ns == 1 && mb <= 1) return fn(StagedCfg<8, 1, 1>{});
+      if (ns == 1 && mb == 2) return fn(StagedCfg<8, 1, 2>{});
+    }
+    if (ty == 16 && mb <= 1) {
+      if (ns == 1) return fn(StagedCfg<16, 1, 1>{});
+      if constexpr (sizeof(ST) == 2) {
+        if (ns == 2) return fn(StagedCfg<16, 2, 1>{});
+      }
     }
   }
-  return cudaErrorInvalidValue;
+  return fallback;
+}
+
+// Resident blocks per SM of the staged kernel for (tile_y, stages, blocks_per_sm).
+template <class ST, class CT>
+cudaError_t staged_occupancy(int ty, int ns, int mb, int *blocks) {
+  return with_staged_cfg<ST>(ty, ns, mb, cudaErrorInvalidValue, [&](auto cfg) {
+    using C = decltype(cfg);
+    return staged_occupancy_one<ST, CT, C::TY, C::NS, C::MINB>(blocks);
+  });
 }
 
 template <class ST, class CT>
 cudaError_t launch_staged(const StepLaunch &l, const StepArgs<CT> &a) {
   if (l.lattice != kD3Q19 || l.stencil != kE4 || a.nx < 32 || a.nx % StagedGeom<ST, 4>::CE != 0)
     return cudaErrorInvalidValue;
-  const int ns = l.stages, mb = l.blocks_per_sm;
-  if (l.tile_y == 4) {
-    if (ns == 2 && mb <= 2) return launch_staged_one<ST, CT, 4, 2, 2>(l, a);
-    if (ns == 2 && mb == 3) return launch_staged_one<ST, CT, 4, 2, 3>(l, a);
-    if (ns == 1 && mb <= 2) return launch_staged_one<ST, CT, 4, 1, 2>(l, a);
-    if (ns == 1 && mb == 3) return launch_staged_one<ST, CT, 4, 1, 3>(l, a);
-  }
-  if constexpr (sizeof(ST) < 8) {
-    if (l.tile_y == 8) {
-      if (ns == 2 && mb <= 1) return launch_staged_one<ST, CT, 8, 2, 1>(l, a);
-      if (ns == 2 && mb == 2) return launch_staged_one<ST, CT, 8, 2, 2>(l, a);
-      if (ns == 1 && mb <= 1) return launch_staged_one<ST, CT, 8, 1, 1>(l, a);
-      if (ns == 1 && mb == 2) return launch_staged_one<ST, CT, 8, 1, 2>(l, a);
-    }
-  }
-  return cudaErrorInvalidValue;
+  return with_staged_cfg<ST>(l.tile_y, l.stages, l.blocks_per_sm, cudaErrorInvalidValue, [&](auto cfg) {
+    using C = decltype(cfg);
+    return launch_staged_one<ST, CT, C::TY, C::NS, C::MINB>(l, a);
+  });
 }
 
 template <int LAT, int STEN, class ST, class CT>
@@ -152,21 +163,10 @@ const void *batched_staged_one(size_t *smem) {
 // Same configurations as launch_staged.
 template <class ST, class CT>
 const void *batched_staged_any(int ty, int ns, int mb, size_t *smem) {
-  if (ty == 4) {
-    if (ns == 2 && mb <= 2) return batched_staged_one<ST, CT, 4, 2, 2>(smem);
-    if (ns == 2 && mb == 3) return batched_staged_one<ST, CT, 4, 2, 3>(smem);
-    if (ns == 1 && mb <= 2) return batched_staged_one<ST, CT, 4, 1, 2>(smem);
-    if (ns == 1 && mb == 3) return batched_staged_one<ST, CT, 4, 1, 3>(smem);
-  }
-  if constexpr (sizeof(ST) < 8) {
-    if (ty == 8) {
-      if (ns == 2 && mb <= 1) return batched_staged_one<ST, CT, 8, 2, 1>(smem);
-      if (ns == 2 && mb == 2) return batched_staged_one<ST, CT, 8, 2, 2>(smem);
-      if (ns == 1 && mb <= 1) return batched_staged_one<ST, CT, 8, 1, 1>(smem);
-      if (ns == 1 && mb == 2) return batched_staged_one<ST, CT, 8, 1, 2>(smem);
-    }
-  }
-  return nullptr;
+  return with_staged_cfg<ST>(ty, ns, mb, static_cast<const void *>(nullptr), [&](auto cfg) {
+    using C = decltype(cfg);
+    return batched_staged_one<ST, CT, C::TY, C::NS, C::MINB>(smem);
+  });
 }
 
 }  // namespace scgb

@@ -29,36 +29,47 @@ def droplet_side(R: float) -> int:
 
 def droplet_sweep(radii, signs, make_fields, params_kw, steps: int, check_every: int = 2048, bin_width=0.5,
                   device="cuda"):
-    """Step one droplet per (R, sign) as a batch and return, per droplet, a dict with the side L, the sign
-    (+1: A-rich, -1: B-rich), R, and from the device: dP, R_s, sigma_s, P_in, P_out, and dP_change =
-    |dP(steps) - dP(steps - check_every)| / dP(steps - check_every) (the convergence measure of section 4).
+    """Step one droplet per (R, sign) in a cube of side droplet_side(R) as a batch; see sweep().
 
     make_fields(shape_zyx, centre_xyz, R, a_rich) -> (n_A, n_B); params_kw: make_params keywords shared by
     every member (storage, G, G_self, tau, psi_self, ...)."""
-    members = [(R, s, droplet_side(R)) for R in radii for s in signs]
-    plist = [B.make_params((L, L, L), **params_kw) for _, _, L in members]
-    fields = [make_fields((L, L, L), (L // 2,) * 3, R, s > 0) for R, s, L in members]
-    batch = B.Batch(plist, fields, device=device)
+    members = []
+    for R in radii:
+        for s in signs:
+            L = droplet_side(R)
+            members.append({"L": L, "R": R, "sign": s, "params": params_kw,
+                            "fields": make_fields((L, L, L), (L // 2,) * 3, R, s > 0)})
+    return sweep(members, steps, check_every, bin_width, device)
+
+
+def sweep(members, steps: int, check_every: int = 2048, bin_width=0.5, device="cuda"):
+    """Step the droplets described by `members` as one batch and return, per member, a dict with its side
+    L, sign (+1: A-rich, -1: B-rich), R and tag, and from the device: dP, R_s, sigma_s, P_in, P_out, and
+    dP_change = |dP(steps) - dP(steps - check_every)| / dP(steps - check_every) (the convergence measure
+    of section 4).  Each member is a dict with L (cube side), R, sign, params (make_params keywords),
+    fields ((n_A, n_B) initial densities) and optionally tag."""
+    plist = [B.make_params((m["L"],) * 3, **m["params"]) for m in members]
+    batch = B.Batch(plist, [m["fields"] for m in members], device=device)
     first = max(0, steps - check_every)
     batch.step(first)
-    before = _analyse(batch, members, bin_width)
+    before = _analyse(batch, [m["L"] for m in members], bin_width)
     batch.step(steps - first)
-    after = _analyse(batch, members, bin_width)
+    after = _analyse(batch, [m["L"] for m in members], bin_width)
     for m in batch.members:
         B.sc_sync(m.ctx)  # raises on a non-finite or non-positive density
     before, after = before.cpu().numpy(), after.cpu().numpy()
     out = []
-    for k, (R, s, L) in enumerate(members):
+    for k, m in enumerate(members):
         o, p = after[k], before[k]
-        out.append({"L": L, "sign": s, "R": R, "dP": float(o[0]), "R_s": float(o[2]), "sigma_s": float(o[3]),
-                    "P_in": float(o[6]), "P_out": float(o[7]),
+        out.append({"L": m["L"], "sign": m["sign"], "R": m["R"], "tag": m.get("tag"), "dP": float(o[0]),
+                    "R_s": float(o[2]), "sigma_s": float(o[3]), "P_in": float(o[6]), "P_out": float(o[7]),
                     "dP_change": float(abs(o[0] - p[0]) / abs(p[0])) if p[0] != 0 else float("nan")})
     return out
 
 
-def _analyse(batch, members, bin_width):
+def _analyse(batch, sides, bin_width):
     outs = []
-    for m, (_, _, L) in zip(batch.members, members):
+    for m, L in zip(batch.members, sides):
         _, o = B.surface_of_tension(m, (L // 2,) * 3, bin_width)
         outs.append(o)
     return torch.stack(outs)
@@ -72,6 +83,24 @@ def flat_sigma0(shape, make_fields, params_kw, steps: int, device="cuda"):
     _, s0 = B.sigma0_flat(sim)
     B.sc_sync(sim.ctx)
     return s0
+
+
+def flat_densities(shape, make_fields, params_kw, steps: int, device="cuda"):
+    """The flat-interface pre-run of section 4: a periodic slab (an A-rich band along z, centred) stepped
+    `steps` times; returns the bulk densities {"A_in", "A_out", "B_in", "B_out"} read at the slab's
+    centre plane (inside the band) and at z = 0 (outside), plus sigma_0 -- the inner and outer values
+    that initialise the droplets of the same couplings."""
+    nA, nB = make_fields(tuple(shape[::-1]))
+    sim = B.Simulation(B.make_params(tuple(shape), **params_kw), nA, nB, device=device)
+    sim.step(steps)
+    a, b, _ = sim.moments(with_u=False)
+    _, s0 = B.sigma0_flat(sim)
+    B.sc_sync(sim.ctx)
+    nx, ny, nz = shape
+    mid, edge = (nz // 2) * nx * ny, 0
+    v = torch.stack([a[mid], a[edge], b[mid], b[edge], s0[0]]).cpu().numpy()
+    return {"A_in": float(v[0]), "A_out": float(v[1]), "B_in": float(v[2]), "B_out": float(v[3]),
+            "sigma0": float(v[4])}
 
 
 def fit(droplets, sigma0=None, order: int = 2, device="cuda"):

@@ -74,6 +74,19 @@ def droplet(shape, centre, radius: float, n_in: float = 0.95, n_out: float = 0.0
     return np.ascontiguousarray(nA), np.ascontiguousarray(nB)
 
 
+def droplet_ab(shape, centre, radius: float, a_in: float, a_out: float, b_in: float, b_out: float,
+               amplitude: float = 1e-3, seed: int = DEFAULT_SEED):
+    """(n_A, n_B) of a droplet with separate inner and outer densities per component (section 4: the
+    values of a flat-interface run); shape = (nz, ny, nx); tanh profile of unit width plus noise."""
+    r = min_image_radius(shape, centre)
+    prof = lambda a, b: 0.5 * (a + b) - 0.5 * (a - b) * np.tanh(r - radius)
+    nA, nB = prof(a_in, a_out), prof(b_in, b_out)
+    if amplitude:
+        nA = nA + noise(shape, amplitude, seed, 0)
+        nB = nB + noise(shape, amplitude, seed, 1)
+    return np.ascontiguousarray(nA), np.ascontiguousarray(nB)
+
+
 def strip_profile(coord: np.ndarray, x0: float, width: float, n_outside: float, n_inside: float) -> np.ndarray:
     """The paper's three-tanh flat-strip profile, as printed, with n_h = n_outside and n_l = n_inside."""
     h, l = n_outside, n_inside

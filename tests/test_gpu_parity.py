@@ -141,7 +141,10 @@ def test_staged_kernel_equals_generic_bitwise(B, storage):
     # tile_z 0: the balanced z split (columns cut into K or K + 1 chunks, 1-D grid)
     configs = [(1, 4, 5, 0, 0), (2, 4, 3, 2, 2), (2, 4, 3, 1, 3), (2, 4, 7, 2, 3), (2, 4, 1, 1, 2), (2, 4, 0, 2, 2)]
     if storage != "F64":
-        configs += [(2, 8, 7, 2, 1), (2, 8, 2, 1, 2), (2, 8, 13, 2, 2), (2, 8, 5, 1, 1), (2, 8, 0, 1, 2)]
+        configs += [(2, 8, 7, 2, 1), (2, 8, 2, 1, 2), (2, 8, 13, 2, 2), (2, 8, 5, 1, 1), (2, 8, 0, 1, 2),
+                    (2, 16, 7, 1, 1), (2, 16, 0, 1, 1)]
+    if storage in ("F16", "BF16"):
+        configs += [(2, 16, 4, 2, 1)]
     for variant, ty, tz, ns, mb in configs:
         sim2 = B.Simulation(B.make_params((96, 19, 13), psi_self=1, storage=st, tau=(1.0, 0.9), G=2.5,
                                           G_self=(-0.4, 0.1), tile_y=ty, tile_z=tz, variant=variant, stages=ns,
