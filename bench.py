@@ -620,7 +620,7 @@ def main():
                     help="run only a study (minutes) and print its JSON line: precision = every result in each "
                          "storage against the FP64 path; paper = Tolman length on the couplings of Eq. self_p")
     ap.add_argument("--study-storage", default="f32", choices=["f64", "f32", "f16", "bf16"])
-    ap.add_argument("--study-density", type=float, default=1.0, help="total density of the paper study")
+    ap.add_argument("--study-density", type=float, default=2.0, help="total density of the paper study")
     ap.add_argument("--study-steps", type=int, default=16384, help="time steps of the Tolman sweep and slab")
     ap.add_argument("--study-size", type=int, default=512, help="side of the large droplet of the study")
     ap.add_argument("--study-size-steps", type=int, default=4096, help="time steps of the large droplet")

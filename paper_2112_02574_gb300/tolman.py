@@ -103,11 +103,26 @@ def flat_densities(shape, make_fields, params_kw, steps: int, device="cuda"):
             "sigma0": float(v[4])}
 
 
-def fit(droplets, sigma0=None, order: int = 2, device="cuda"):
-    """Eq. sigma_c over the droplets of droplet_sweep (R_s signed by the droplet's component), on the
-    device; sigma0 a CUDA tensor [1] (held fixed) or None (fitted).  Returns a dict sigma0, delta,
-    rigidity (2 kbar + k), rms."""
-    Rs = torch.tensor([d["sign"] * d["R_s"] for d in droplets], dtype=torch.float64, device=device)
-    sg = torch.tensor([d["sigma_s"] for d in droplets], dtype=torch.float64, device=device)
+def usable(d, max_change: float = 1e-3) -> bool:
+    """A droplet enters the fit if it is one: a positive pressure jump and a positive surface-of-tension
+    radius within a factor two of its initial radius, and dP settled to max_change over the last check
+    interval (section 4 converges to 1e-5; a droplet that dissolved or whose interface fills the box
+    fails one of these)."""
+    ok = d["dP"] > 0 and 0.5 * d["R"] < d["R_s"] < 2.0 * d["R"]
+    return bool(ok and d["dP_change"] < max_change)
+
+
+def fit(droplets, sigma0=None, order: int = 2, device="cuda", select=usable):
+    """Eq. sigma_c over the droplets of sweep() that pass `select` (R_s signed by the droplet's component),
+    on the device; sigma0 a CUDA tensor [1] (held fixed) or None (fitted).  Returns a dict sigma0, delta,
+    rigidity (2 kbar + k), rms, used (droplets in the fit)."""
+    ds = [d for d in droplets if select is None or select(d)]
+    need = order + (0 if sigma0 is not None else 1)
+    if len(ds) < need:
+        return {"sigma0": float("nan"), "delta": float("nan"), "rigidity": float("nan"), "rms": float("nan"),
+                "used": len(ds)}
+    Rs = torch.tensor([d["sign"] * d["R_s"] for d in ds], dtype=torch.float64, device=device)
+    sg = torch.tensor([d["sigma_s"] for d in ds], dtype=torch.float64, device=device)
     o = B.curvature_fit(Rs, sg, order=order, sigma0=sigma0).cpu().numpy()
-    return {"sigma0": float(o[0]), "delta": float(o[1]), "rigidity": float(o[2]), "rms": float(o[3])}
+    return {"sigma0": float(o[0]), "delta": float(o[1]), "rigidity": float(o[2]), "rms": float(o[3]),
+            "used": len(ds)}
