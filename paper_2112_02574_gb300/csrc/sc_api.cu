@@ -77,9 +77,21 @@ int default_tile_y(const sc_params *p) {
   if (use_staged(p)) return staged_default_tile_y(p);
   return p->lattice == SC_D3Q19 ? 8 : 4;
 }
-int effective_stages(const sc_params *p, int tile_y) { return p->stages ? p->stages : (tile_y == 4 ? 2 : 1); }
+// F32 with a self coupling (the psi ring and the self term make the block heavier):
+// one stage and three resident blocks per SM beat two stages and two blocks at every
+// size measured (128^3 .. 512^3); without one, two stages and two blocks.
+bool has_self(const sc_params *p) { return p->G_self[0] != 0.0 || p->G_self[1] != 0.0; }
+bool f32_self_config(const sc_params *p, int tile_y) {
+  return p->storage == SC_STORE_F32 && tile_y == 4 && has_self(p);
+}
+int effective_stages(const sc_params *p, int tile_y) {
+  if (p->stages) return p->stages;
+  if (f32_self_config(p, tile_y)) return 1;
+  return tile_y == 4 ? 2 : 1;
+}
 int effective_blocks_per_sm(const sc_params *p, int tile_y) {
   if (p->blocks_per_sm) return p->blocks_per_sm;
+  if (f32_self_config(p, tile_y)) return 3;
   return tile_y == 16 ? 1 : (tile_y == 8 ? 2 : (is_16bit(p->storage) ? 3 : 2));
 }
 int default_tile_z(const sc_params *p) {
@@ -319,14 +331,15 @@ StepArgs<CT> step_args(sc_ctx *c) {
 sc_status plan_balanced_split(sc_ctx *c) {
   constexpr int kTargetChunk = 24;
   int dev = 0, sms = 0, occ = 0;
+  const bool self_on = has_self(&c->p);
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) {
     switch (c->p.storage) {
-      case SC_STORE_F32: e = staged_occupancy_f32(c->tile_y, c->stages, c->blocks_per_sm, &occ); break;
-      case SC_STORE_F16: e = staged_occupancy_f16(c->tile_y, c->stages, c->blocks_per_sm, &occ); break;
-      case SC_STORE_BF16: e = staged_occupancy_bf16(c->tile_y, c->stages, c->blocks_per_sm, &occ); break;
-      default: e = staged_occupancy_f64(c->tile_y, c->stages, c->blocks_per_sm, &occ); break;
+      case SC_STORE_F32: e = staged_occupancy_f32(c->tile_y, c->stages, c->blocks_per_sm, self_on, &occ); break;
+      case SC_STORE_F16: e = staged_occupancy_f16(c->tile_y, c->stages, c->blocks_per_sm, self_on, &occ); break;
+      case SC_STORE_BF16: e = staged_occupancy_bf16(c->tile_y, c->stages, c->blocks_per_sm, self_on, &occ); break;
+      default: e = staged_occupancy_f64(c->tile_y, c->stages, c->blocks_per_sm, self_on, &occ); break;
     }
   }
   if (e != cudaSuccess) return fail(SC_ECUDA, "occupancy of the staged kernel: %s", cudaGetErrorString(e));
@@ -738,9 +751,25 @@ bool batch_staged(int32_t n, const sc_params *params) {
     if (!use_staged(&params[k])) return false;
   return true;
 }
-sc_params member_params(const sc_params &p, bool staged) {
-  sc_params q = p;
+// Member k's parameters as the batch steps it: the kernel variant of the batch and,
+// where the member leaves them to the library, stages and blocks_per_sm resolved
+// once for the whole batch (a self coupling in any member chooses the self-coupling
+// configuration for all, since every member runs in the same launch).
+sc_params member_params(int32_t n, const sc_params *params, int k, bool staged) {
+  sc_params q = params[k];
   q.variant = staged ? 2 : 1;
+  sc_params rep = params[0];
+  rep.variant = q.variant;
+  for (int j = 0; j < n; ++j)
+    if (has_self(&params[j])) {
+      rep.G_self[0] = params[j].G_self[0];
+      rep.G_self[1] = params[j].G_self[1];
+    }
+  rep.stages = 0;
+  rep.blocks_per_sm = 0;
+  const int ty = default_tile_y(&q);
+  if (!q.stages) q.stages = effective_stages(&rep, ty);
+  if (!q.blocks_per_sm) q.blocks_per_sm = effective_blocks_per_sm(&rep, ty);
   return q;
 }
 
@@ -748,7 +777,7 @@ size_t batch_table_bytes(int32_t n, const sc_params *params, int *nitems_out) {
   const bool staged = batch_staged(n, params);
   int nitems = 0;
   for (int k = 0; k < n; ++k) {
-    const sc_params q = member_params(params[k], staged);
+    const sc_params q = member_params(n, params, k, staged);
     const int ty = default_tile_y(&q), tz = default_tile_z(&q);
     nitems += ((q.nx + 31) / 32) * ((q.ny + ty - 1) / ty) * ((q.nz + tz - 1) / tz);
   }
@@ -764,12 +793,12 @@ sc_status batch_validate(int32_t n, const sc_params *params) {
     if (st != SC_OK) return st;
   }
   const bool staged = batch_staged(n, params);
-  const sc_params a = member_params(params[0], staged);
+  const sc_params a = member_params(n, params, 0, staged);
   const int tya = default_tile_y(&a);
   for (int k = 0; k < n; ++k) {
     if (!staged && params[k].variant == 2)
       return fail(SC_EINVAL, "lattice %d asks for the staged kernel, which not every member of the batch can take", k);
-    const sc_params b = member_params(params[k], staged);
+    const sc_params b = member_params(n, params, k, staged);
     const int tyb = default_tile_y(&b);
     if (a.lattice != b.lattice || a.stencil != b.stencil || a.storage != b.storage || tya != tyb)
       return fail(SC_EINVAL, "all lattices of a batch share lattice, stencil, storage and tile_y");
@@ -813,7 +842,7 @@ sc_status sc_batch_create(int32_t n, const sc_params *params, const double *cons
   size_t off = 0;
   const bool staged = batch_staged(n, params);
   for (int k = 0; k < n; ++k) {
-    sc_params pk = member_params(params[k], staged);
+    sc_params pk = member_params(n, params, k, staged);
     const size_t bytes = layout_of(&pk).total;
     st = sc_create(&pk, nA0[k], nB0[k], ws + off, bytes, stream, &b->ctx[k]);
     if (st != SC_OK) {
@@ -874,11 +903,13 @@ sc_status sc_batch_create(int32_t n, const sc_params *params, const double *cons
   b->staged = staged ? 1 : 0;
   if (staged) {
     const int ns = b->ctx[0]->stages, mb = b->ctx[0]->blocks_per_sm;
+    bool any_self = false;
+    for (int k = 0; k < n; ++k) any_self = any_self || has_self(&params[k]);
     switch (storage) {
-      case SC_STORE_F32: b->kernel = batched_staged_kernel_f32(b->tile_y, ns, mb, &b->smem); break;
-      case SC_STORE_F16: b->kernel = batched_staged_kernel_f16(b->tile_y, ns, mb, &b->smem); break;
-      case SC_STORE_BF16: b->kernel = batched_staged_kernel_bf16(b->tile_y, ns, mb, &b->smem); break;
-      default: b->kernel = batched_staged_kernel_f64(b->tile_y, ns, mb, &b->smem); break;
+      case SC_STORE_F32: b->kernel = batched_staged_kernel_f32(b->tile_y, ns, mb, any_self, &b->smem); break;
+      case SC_STORE_F16: b->kernel = batched_staged_kernel_f16(b->tile_y, ns, mb, any_self, &b->smem); break;
+      case SC_STORE_BF16: b->kernel = batched_staged_kernel_bf16(b->tile_y, ns, mb, any_self, &b->smem); break;
+      default: b->kernel = batched_staged_kernel_f64(b->tile_y, ns, mb, any_self, &b->smem); break;
     }
   } else {
     switch (storage) {

@@ -34,17 +34,19 @@ const void *batched_kernel_f16(int lattice, int stencil, int tile_y, size_t *sme
 const void *batched_kernel_bf16(int lattice, int stencil, int tile_y, size_t *smem);
 const void *batched_kernel_f64(int lattice, int stencil, int tile_y, size_t *smem);
 
-// Resident blocks per SM of the staged step kernel for (tile_y, stages, blocks_per_sm).
-cudaError_t staged_occupancy_f32(int tile_y, int stages, int blocks_per_sm, int *blocks);
-cudaError_t staged_occupancy_f16(int tile_y, int stages, int blocks_per_sm, int *blocks);
-cudaError_t staged_occupancy_bf16(int tile_y, int stages, int blocks_per_sm, int *blocks);
-cudaError_t staged_occupancy_f64(int tile_y, int stages, int blocks_per_sm, int *blocks);
+// Resident blocks per SM of the staged step kernel for (tile_y, stages, blocks_per_sm),
+// with or without the psi ring of a self coupling.
+cudaError_t staged_occupancy_f32(int tile_y, int stages, int blocks_per_sm, bool self_on, int *blocks);
+cudaError_t staged_occupancy_f16(int tile_y, int stages, int blocks_per_sm, bool self_on, int *blocks);
+cudaError_t staged_occupancy_bf16(int tile_y, int stages, int blocks_per_sm, bool self_on, int *blocks);
+cudaError_t staged_occupancy_f64(int tile_y, int stages, int blocks_per_sm, bool self_on, int *blocks);
 
 // The batched staged step kernel (D3Q19, E4) for (tile_y, stages, blocks_per_sm),
-// same parameters and block shape as above; nullptr if not instantiated.
-const void *batched_staged_kernel_f32(int tile_y, int stages, int blocks_per_sm, size_t *smem);
-const void *batched_staged_kernel_f16(int tile_y, int stages, int blocks_per_sm, size_t *smem);
-const void *batched_staged_kernel_bf16(int tile_y, int stages, int blocks_per_sm, size_t *smem);
-const void *batched_staged_kernel_f64(int tile_y, int stages, int blocks_per_sm, size_t *smem);
+// same parameters and block shape as above; nullptr if not instantiated.  self_on:
+// some member has a self coupling (the psi ring is then part of *smem).
+const void *batched_staged_kernel_f32(int tile_y, int stages, int blocks_per_sm, bool self_on, size_t *smem);
+const void *batched_staged_kernel_f16(int tile_y, int stages, int blocks_per_sm, bool self_on, size_t *smem);
+const void *batched_staged_kernel_bf16(int tile_y, int stages, int blocks_per_sm, bool self_on, size_t *smem);
+const void *batched_staged_kernel_f64(int tile_y, int stages, int blocks_per_sm, bool self_on, size_t *smem);
 
 }  // namespace scgb

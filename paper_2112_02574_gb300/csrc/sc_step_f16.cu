@@ -4,9 +4,10 @@ cudaError_t scgb::launch_step_f16(const StepLaunch &l, const StepArgs<float> &a)
 const void *scgb::batched_kernel_f16(int lattice, int stencil, int tile_y, size_t *smem) {
   return batched_any<__half, float>(lattice, stencil, tile_y, smem);
 }
-const void *scgb::batched_staged_kernel_f16(int tile_y, int stages, int blocks_per_sm, size_t *smem) {
-  return batched_staged_any<__half, float>(tile_y, stages, blocks_per_sm, smem);
+const void *scgb::batched_staged_kernel_f16(int tile_y, int stages, int blocks_per_sm, bool self_on,
+                                             size_t *smem) {
+  return batched_staged_any<__half, float>(tile_y, stages, blocks_per_sm, self_on, smem);
 }
-cudaError_t scgb::staged_occupancy_f16(int tile_y, int stages, int blocks_per_sm, int *blocks) {
-  return staged_occupancy<__half, float>(tile_y, stages, blocks_per_sm, blocks);
+cudaError_t scgb::staged_occupancy_f16(int tile_y, int stages, int blocks_per_sm, bool self_on, int *blocks) {
+  return staged_occupancy<__half, float>(tile_y, stages, blocks_per_sm, self_on, blocks);
 }

@@ -25,11 +25,12 @@ cudaError_t launch_one(const StepLaunch &l, const StepArgs<CT> &a) {
 // Staged kernel: one block per (x column, y column, z chunk), like the generic kernel.
 template <class ST, class CT, int TY, int NS, int MINB>
 cudaError_t launch_staged_one(const StepLaunch &l, const StepArgs<CT> &a) {
-  constexpr size_t smem = staged_smem_bytes<ST, CT, TY, NS>();
+  constexpr size_t smem_max = staged_smem_bytes<ST, CT, TY, NS>();
+  const size_t smem = staged_smem_bytes<ST, CT, TY, NS>(a.self_on != 0);
   auto *k = sc_step_staged<ST, CT, TY, NS, MINB>;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_max));
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -40,12 +41,13 @@ cudaError_t launch_staged_one(const StepLaunch &l, const StepArgs<CT> &a) {
 }
 
 template <class ST, class CT, int TY, int NS, int MINB>
-cudaError_t staged_occupancy_one(int *blocks) {
-  constexpr size_t smem = staged_smem_bytes<ST, CT, TY, NS>();
+cudaError_t staged_occupancy_one(bool self_on, int *blocks) {
   auto *k = sc_step_staged<ST, CT, TY, NS, MINB>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  cudaError_t e =
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(staged_smem_bytes<ST, CT, TY, NS>()));
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, 32 * TY, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, 32 * TY,
+                                                       staged_smem_bytes<ST, CT, TY, NS>(self_on));
 }
 
 // One instantiated staged configuration, as a tag type.
@@ -86,10 +88,10 @@ R with_staged_cfg(int ty, int ns, int mb, R fallback, Fn &&fn) {
 
 // Resident blocks per SM of the staged kernel for (tile_y, stages, blocks_per_sm).
 template <class ST, class CT>
-cudaError_t staged_occupancy(int ty, int ns, int mb, int *blocks) {
+cudaError_t staged_occupancy(int ty, int ns, int mb, bool self_on, int *blocks) {
   return with_staged_cfg<ST>(ty, ns, mb, cudaErrorInvalidValue, [&](auto cfg) {
     using C = decltype(cfg);
-    return staged_occupancy_one<ST, CT, C::TY, C::NS, C::MINB>(blocks);
+    return staged_occupancy_one<ST, CT, C::TY, C::NS, C::MINB>(self_on, blocks);
   });
 }
 
@@ -152,20 +154,21 @@ const void *batched_any(int lat, int sten, int ty, size_t *smem) {
 }
 
 template <class ST, class CT, int TY, int NS, int MINB>
-const void *batched_staged_one(size_t *smem) {
-  constexpr size_t bytes = staged_smem_bytes<ST, CT, TY, NS>();
+const void *batched_staged_one(bool self_on, size_t *smem) {
   auto *k = sc_step_staged_batched<ST, CT, TY, NS, MINB>;
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)) != cudaSuccess) return nullptr;
-  *smem = bytes;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(staged_smem_bytes<ST, CT, TY, NS>())) != cudaSuccess)
+    return nullptr;
+  *smem = staged_smem_bytes<ST, CT, TY, NS>(self_on);
   return reinterpret_cast<const void *>(k);
 }
 
 // Same configurations as launch_staged.
 template <class ST, class CT>
-const void *batched_staged_any(int ty, int ns, int mb, size_t *smem) {
+const void *batched_staged_any(int ty, int ns, int mb, bool self_on, size_t *smem) {
   return with_staged_cfg<ST>(ty, ns, mb, static_cast<const void *>(nullptr), [&](auto cfg) {
     using C = decltype(cfg);
-    return batched_staged_one<ST, CT, C::TY, C::NS, C::MINB>(smem);
+    return batched_staged_one<ST, CT, C::TY, C::NS, C::MINB>(self_on, smem);
   });
 }
 

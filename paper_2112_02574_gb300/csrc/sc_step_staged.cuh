@@ -64,12 +64,13 @@ struct StagedGeom {
   template <int NS> __host__ __device__ static constexpr size_t at_ring() { return at_rowcz<NS>() + sizeof(int) * ((NROW + 3) & ~3); }
 };
 
-// Shared memory of one block (the carve-up above, for NS population stages, plus
-// two rings of NPL planes).
+// Shared memory of one block: the carve-up above, for NS population stages, plus
+// the density ring and, with a self coupling (self_on), the psi ring; without
+// one the psi ring is never touched and is left out of the launch.
 template <class ST, class CT, int TY, int NS>
-constexpr size_t staged_smem_bytes() {
+constexpr size_t staged_smem_bytes(bool self_on = true) {
   using G = StagedGeom<ST, TY>;
-  return G::template at_ring<NS>() + sizeof(P2<CT>) * 2 * G::NPL * G::PLANE;
+  return G::template at_ring<NS>() + sizeof(P2<CT>) * (self_on ? 2 : 1) * G::NPL * G::PLANE;
 }
 
 // Sum of the Q staged population pairs arriving at tile position (px, py), in
@@ -116,7 +117,8 @@ __device__ __forceinline__ void staged_block(const StepArgs<CT> &a, int bx, int 
   int64_t *rowbase = reinterpret_cast<int64_t *>(smem_raw + G::template at_rowbase<NS>());    // [NROW]
   int *rowcz = reinterpret_cast<int *>(smem_raw + G::template at_rowcz<NS>());                // [NROW]
   P2<CT> *s_dn = reinterpret_cast<P2<CT> *>(smem_raw + G::template at_ring<NS>());            // [NPL][PLANE]
-  P2<CT> *s_psi = s_dn + G::NPL * G::PLANE;                                     // [NPL][PLANE]
+  // [NPL][PLANE]; only read or written under a.self_on (else it aliases s_dn, untouched)
+  P2<CT> *s_psi = s_dn + (a.self_on ? G::NPL * G::PLANE : 0);
 
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   const int nx = a.nx, ny = a.ny, nz = a.nz;

@@ -158,17 +158,20 @@ def test_staged_kernel_equals_generic_bitwise(B, storage):
 
 
 @pytest.mark.parametrize("storage", ["F32", "F16"])
-def test_balanced_z_split_equals_generic(B, storage):
+@pytest.mark.parametrize("G_self", [(-0.4, 0.0), (0.0, 0.0)])
+def test_balanced_z_split_equals_generic(B, storage, G_self):
     """A box whose balanced split gives columns of unequal chunk counts (on a
-    152-SM GPU with two resident blocks per SM: 304 blocks over 30 columns in
-    FP32, K = 10 with 4 columns of 11 chunks; over 15 columns in FP16, K = 20):
-    same state as the generic kernel, bit for bit."""
+    152-SM GPU: FP32 without a self coupling 304 blocks over 30 columns, K = 10
+    with 4 columns of 11 chunks; FP32 with one, three blocks per SM, 456 blocks,
+    K = 15 with 6 columns of 16; FP16 304 blocks over 15 columns, K = 20):
+    same state as the generic kernel, bit for bit; with and without a self
+    coupling (without one the staged launch leaves the psi ring out)."""
     st = getattr(B, f"SC_STORE_{storage}")
     shape = (96, 40, 128)
     f = S.droplet(shape[::-1], (48, 20, 64), 12.0, n_in=0.85, n_out=0.15, amplitude=1e-3)
     outs = []
     for variant, tz in ((1, 32), (2, 0)):
-        sim = B.Simulation(B.make_params(shape, psi_self=1, storage=st, G=2.5, G_self=(-0.4, 0.0), tile_z=tz,
+        sim = B.Simulation(B.make_params(shape, psi_self=1, storage=st, G=2.5, G_self=G_self, tile_z=tz,
                                          variant=variant), *f)
         sim.step(5)
         sim.sync()
