@@ -556,8 +556,9 @@ def paper_couplings(dGAB: float, dGc: float = 0.4):
 def paper_tolman_study(args, dev):
     """The Tolman sweep on the paper's couplings (section 4): per dG_AB a flat-interface pre-run (slab
     16 x 16 x 128) gives the bulk densities and sigma_0; A-rich and B-rich droplets of side L (odd, the
-    paper's sizes) and R = L / 4 start from those densities; all droplets of all dG_AB run as one batch;
-    Eq. sigma_c is fitted on the device with sigma_0 held at the slab value."""
+    paper's sizes) and R = L / 4 start from those densities; all droplets of all dG_AB run as one batch
+    until each has converged by section 4's criteria (then it retires from the batch); Eq. sigma_c is
+    fitted on the device with sigma_0 held at the slab value."""
     import sc_synth
     from paper_2112_02574_gb300 import binding as B
     from paper_2112_02574_gb300 import tolman
@@ -583,8 +584,10 @@ def paper_tolman_study(args, dev):
                                         outside[1], amplitude=1e-3)
                 members.append({"L": L, "R": L / 4.0, "sign": sign, "params": kw, "fields": f, "tag": d})
     t0 = time.perf_counter()
-    drops = tolman.sweep(members, T, device=dev)
+    drops = tolman.sweep(members, T, device=dev, converge=True)
     out["sweep_seconds"] = time.perf_counter() - t0
+    out["convergence"] = "section 4: every 2048 steps, |dP change| / dP < 1e-5 or dU < 1e-12; converged " \
+                         "droplets retire from the batch; at most --study-steps steps"
     import torch
 
     for d in PAPER_DGAB:
@@ -592,6 +595,10 @@ def paper_tolman_study(args, dev):
         s0 = torch.tensor([flats[d]["sigma0"]], dtype=torch.float64, device=dev)
         out["sets"][f"{d:+.2f}"] = {"flat": flats[d], "fit_fixed_sigma0": tolman.fit(ds, s0, device=dev),
                                     "fit_free_sigma0": tolman.fit(ds, None, device=dev),
+                                    "converged": sum(1 for x in ds if x["converged"]),
+                                    "steps_range": [min(x["steps"] for x in ds), max(x["steps"] for x in ds)],
+                                    "max_com_offset": max(x["com_offset"] for x in ds),
+                                    "com_accepted": sum(1 for x in ds if x["com_offset"] < 1e-3),
                                     "max_dP_change": max(x["dP_change"] for x in ds), "droplets": ds}
     print(json.dumps(out), flush=True)
 

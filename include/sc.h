@@ -165,6 +165,22 @@ sc_status sc_bulk_pressure_at(sc_ctx *ctx, const int32_t node[3], double *out);
 sc_status sc_sigma_minimum(const double *rows, int32_t nbins, const double *P_in_out, int32_t dim, double R_lo,
                            double R_hi, double R_step, double *out, void *stream);
 
+/* Convergence measure of section 4 on the velocity field: dU = (1 / N) sum over
+ * the sites x of sum_alpha |u_alpha(x) - u_prev_alpha(x)|, with u the common
+ * velocity of Eq. u (force included) of the current state; u_prev is then
+ * overwritten with u, ready for the next interval.  u_prev: device FP64 [3][N]
+ * (e.g. from sc_moments at the start of the interval); out: device FP64 [1].
+ * Deterministic; asynchronous on the context's stream. */
+sc_status sc_velocity_change(sc_ctx *ctx, double *u_prev, double *out);
+
+/* Centre of mass of component `component` (0: A, 1: B) counted as its density
+ * excess over `background`: w(x) = n_J(x) - background, out = (sum w x / W,
+ * sum w y / W, sum w z / W, W) in lattice coordinates (no periodic unwrapping:
+ * for a droplet away from the box faces, the acceptance test of section 4
+ * compares this with the centre node).  out: device FP64 [4].  Deterministic;
+ * asynchronous on the context's stream. */
+sc_status sc_centre_of_mass(sc_ctx *ctx, int32_t component, double background, double *out);
+
 /* Flat-interface surface tension (section 4, the sigma_0 of Eq. sigma_c):
  * sigma_0 = sum over the planes z >= nbins / 2 of P_N(z) - P_T(z), from the rows
  * of a PLANAR_Z profile (one bin per plane) of a periodic slab whose second
@@ -247,6 +263,15 @@ sc_ctx *sc_batch_member(sc_batch *batch, int32_t k);
 int64_t sc_batch_launches(const sc_batch *batch);
 /* Step kernel of the batch: 1 generic, 2 staged (0 for NULL). */
 int32_t sc_batch_variant(const sc_batch *batch);
+/* Stop stepping member k (section 4 runs each droplet until it has converged,
+ * so members of a sweep finish at different times).  The member keeps its state
+ * and step count and stays usable for the analysis entry points; later
+ * sc_batch_step calls launch over the remaining members only (work list and
+ * graph rebuilt here).  Retiring a retired member does nothing.  Synchronises
+ * the batch's stream. */
+sc_status sc_batch_retire(sc_batch *batch, int32_t k);
+/* Members still stepped (not retired). */
+int32_t sc_batch_active(const sc_batch *batch);
 void sc_batch_destroy(sc_batch *batch);
 
 /* The step kernel this context launches: out[0..8) = variant (1 generic, 2

@@ -86,6 +86,10 @@ def _load():
         "sc_batch_member": (V, [V, I32]),
         "sc_batch_launches": (I64, [V]),
         "sc_batch_variant": (I32, [V]),
+        "sc_batch_retire": (I32, [V, I32]),
+        "sc_batch_active": (I32, [V]),
+        "sc_velocity_change": (I32, [V, V, V]),
+        "sc_centre_of_mass": (I32, [V, I32, D, V]),
         "sc_batch_destroy": (None, [V]),
         "sc_reference_density": (I32, [V, ctypes.POINTER(D)]),
         "sc_destroy": (None, [V]),
@@ -248,6 +252,22 @@ def sc_batch_variant(batch) -> int:
     return lib.sc_batch_variant(batch)
 
 
+def sc_batch_retire(batch, k):
+    _check(lib.sc_batch_retire(batch, int(k)))
+
+
+def sc_batch_active(batch) -> int:
+    return lib.sc_batch_active(batch)
+
+
+def sc_velocity_change(ctx, u_prev, out):
+    _check(lib.sc_velocity_change(ctx, _ptr(u_prev), _ptr(out)))
+
+
+def sc_centre_of_mass(ctx, component, background, out):
+    _check(lib.sc_centre_of_mass(ctx, int(component), float(background), _ptr(out)))
+
+
 def sc_batch_destroy(batch):
     lib.sc_batch_destroy(batch)
 
@@ -348,6 +368,19 @@ class Simulation:
         sc_bulk_pressure_at(self.ctx, node, out)
         return out
 
+    def velocity_change(self, u_prev):
+        """Section 4's velocity criterion since u_prev (CUDA float64 [3][N], updated in place):
+        a CUDA tensor [1] with (1/N) sum_x sum_alpha |u_alpha - u_prev_alpha|."""
+        out = torch.empty(1, dtype=torch.float64, device=self.device)
+        sc_velocity_change(self.ctx, u_prev, out)
+        return out
+
+    def centre_of_mass(self, component: int, background: float):
+        """(X, Y, Z, W) of component 0 (A) or 1 (B) counted above `background`: a CUDA tensor [4]."""
+        out = torch.empty(4, dtype=torch.float64, device=self.device)
+        sc_centre_of_mass(self.ctx, component, background, out)
+        return out
+
     def totals(self):
         out = torch.empty(5, dtype=torch.float64, device=self.device)
         sc_totals(self.ctx, out)
@@ -418,6 +451,14 @@ class Batch:
     def staged(self) -> bool:
         """True when the batch steps with the staged kernel."""
         return sc_batch_variant(self.handle) == 2
+
+    def retire(self, k: int):
+        """Stop stepping member k (it keeps its state for analysis)."""
+        sc_batch_retire(self.handle, k)
+
+    @property
+    def active(self) -> int:
+        return sc_batch_active(self.handle)
 
 
 def surface_of_tension(sim: Simulation, centre, bin_width=0.5, nbins=None, in_node=None, out_node=None,

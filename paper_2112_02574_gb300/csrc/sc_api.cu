@@ -203,6 +203,8 @@ struct sc_batch {
   int nitems;
   int tile_y;
   int staged;         // members step with the staged kernel
+  char *retired;      // retired[k]: member k is no longer stepped
+  int active;         // members still stepped
   const void *kernel;
   size_t smem;
   cudaGraph_t graph;
@@ -324,12 +326,12 @@ StepArgs<CT> step_args(sc_ctx *c) {
 // Balanced z split of the staged kernel (tile_z left to the library, and a plain grid
 // of tile_z chunks would fill fewer than four waves of the GPU): the grid is
 // exactly waves x (SMs x resident blocks per SM) blocks, with waves chosen for
-// z-chunks of about kTargetChunk planes, and every column of 32 x tile_y sites is
+// z-chunks of about kTargetChunk planes (wave count rounded to nearest), and every column of 32 x tile_y sites is
 // cut into K or K + 1 equal z-chunks.  A fixed tile_z instead leaves a partly empty
 // last wave whenever the block count is not a multiple of the resident slots (at
 // 128^3: 256 blocks of 32 planes for 304 slots).
 sc_status plan_balanced_split(sc_ctx *c) {
-  constexpr int kTargetChunk = 24;
+  constexpr int kTargetChunk = 18;  // 128^3 F32: 3 waves of 18-plane chunks beat 2 waves of 26 (+2 %)
   int dev = 0, sms = 0, occ = 0;
   const bool self_on = has_self(&c->p);
   cudaError_t e = cudaGetDevice(&dev);
@@ -347,7 +349,7 @@ sc_status plan_balanced_split(sc_ctx *c) {
   const int64_t nz = c->p.nz, slots = (int64_t)sms * (occ > 0 ? occ : 1);
   const int64_t fixed_blocks = cols * ((nz + c->tile_z - 1) / c->tile_z);
   if (fixed_blocks >= 4 * slots) return SC_OK;  // many waves: the plain grid's last-wave loss is small
-  int64_t waves = cols * nz / (slots * kTargetChunk);
+  int64_t waves = (2 * cols * nz + slots * kTargetChunk) / (2 * slots * kTargetChunk);  // rounded
   if (waves < 1) waves = 1;
   int64_t G = slots * waves;
   const int64_t gmax = cols * (nz / 4 > 1 ? nz / 4 : 1);  // chunks of 4 planes or more
@@ -554,6 +556,50 @@ sc_status sc_moments(sc_ctx *c, double *nA, double *nB, double *u) {
 #undef SC_VEL
     SC_CUDA(cudaGetLastError());
   }
+  return SC_OK;
+}
+
+sc_status sc_velocity_change(sc_ctx *c, double *u_prev, double *out) {
+  if (!c || !u_prev || !out) return fail(SC_EINVAL, "ctx, u_prev and out must be non-NULL");
+  sc_status st = ensure_fields(c);
+  if (st != SC_OK) return st;
+  PopArgs a = pop_args(c, c->cur);
+  ForceParams fp = force_params(c);
+  const double *F = fields_of(c);
+  double *part = partial_of(c);
+  const int blocks = grid_for(c->N, 256) < kMaxPartialBlocks ? grid_for(c->N, 256) : kMaxPartialBlocks;
+  const int lat = c->p.lattice, sten = c->p.stencil, s = c->p.storage;
+#define SC_DU(LAT, STEN, ST) \
+  velocity_change_partial_kernel<LAT, STEN, ST><<<blocks, 256, 0, c->stream>>>(a, fp, F, u_prev, part)
+#define SC_DU_ST(LAT, STEN)                                   \
+  do {                                                        \
+    if (s == SC_STORE_F32) SC_DU(LAT, STEN, float);           \
+    if (s == SC_STORE_F16) SC_DU(LAT, STEN, __half);          \
+    if (s == SC_STORE_BF16) SC_DU(LAT, STEN, __nv_bfloat16);  \
+    if (s == SC_STORE_F64) SC_DU(LAT, STEN, double);          \
+  } while (0)
+  if (lat == SC_D3Q19 && sten == SC_FORCE_E4) SC_DU_ST(kD3Q19, kE4);
+  if (lat == SC_D3Q19 && sten == SC_FORCE_E6) SC_DU_ST(kD3Q19, kE6);
+  if (lat == SC_D2Q9) SC_DU_ST(kD2Q9, kE4);
+#undef SC_DU_ST
+#undef SC_DU
+  finalize_measure_kernel<<<1, 32, 0, c->stream>>>(part, blocks, 0, 1.0 / double(c->N), out);
+  SC_CUDA(cudaGetLastError());
+  return SC_OK;
+}
+
+sc_status sc_centre_of_mass(sc_ctx *c, int32_t component, double background, double *out) {
+  if (!c || !out) return fail(SC_EINVAL, "ctx and out must be non-NULL");
+  if (component != 0 && component != 1) return fail(SC_EINVAL, "component must be 0 (A) or 1 (B)");
+  if (!isfinite(background)) return fail(SC_EINVAL, "background must be finite");
+  sc_status st = ensure_fields(c);
+  if (st != SC_OK) return st;
+  const int blocks = grid_for(c->N, 256) < kMaxPartialBlocks ? grid_for(c->N, 256) : kMaxPartialBlocks;
+  double *part = partial_of(c);
+  com_partial_kernel<<<blocks, 256, 0, c->stream>>>(fields_of(c) + (int64_t)component * c->N, c->p.nx, c->p.ny, c->N,
+                                                    background, part);
+  finalize_measure_kernel<<<1, 32, 0, c->stream>>>(part, blocks, 1, 1.0, out);
+  SC_CUDA(cudaGetLastError());
   return SC_OK;
 }
 
@@ -810,6 +856,69 @@ sc_status batch_validate(int32_t n, const sc_params *params) {
 }
 }  // namespace
 
+namespace {
+// The work list of the members still stepped, (member, x tile, y tile, z chunk) per block,
+// uploaded to the batch's item table (synchronously: no launch of the batch is in flight).
+sc_status batch_upload_items(sc_batch *b) {
+  int total = 0;
+  for (int k = 0; k < b->n; ++k) {
+    if (b->retired[k]) continue;
+    const sc_ctx *c = b->ctx[k];
+    total += ((c->p.nx + 31) / 32) * ((c->p.ny + c->tile_y - 1) / c->tile_y) * ((c->p.nz + c->tile_z - 1) / c->tile_z);
+  }
+  b->nitems = total;
+  if (total == 0) return SC_OK;
+  int4 *items = new (std::nothrow) int4[total];
+  if (!items) return fail(SC_ENOMEM, "host allocation failed");
+  int m = 0;
+  for (int k = 0; k < b->n; ++k) {
+    if (b->retired[k]) continue;
+    const sc_ctx *c = b->ctx[k];
+    const int gx = (c->p.nx + 31) / 32, gy = (c->p.ny + c->tile_y - 1) / c->tile_y,
+              gz = (c->p.nz + c->tile_z - 1) / c->tile_z;
+    for (int z = 0; z < gz; ++z)
+      for (int y = 0; y < gy; ++y)
+        for (int x = 0; x < gx; ++x) items[m++] = make_int4(k, x, y, z);
+  }
+  cudaError_t e = cudaMemcpyAsync(b->items_dev, items, sizeof(int4) * total, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  delete[] items;
+  if (e != cudaSuccess) return fail(SC_ECUDA, "uploading the batch work list: %s", cudaGetErrorString(e));
+  return SC_OK;
+}
+
+// A graph of kGraphSteps chained launches over the current work list, swap = 0, 1, 0, 1, ...
+// (none when no member is left).
+sc_status batch_build_graph(sc_batch *b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  if (b->nitems == 0) return SC_OK;
+  cudaError_t e = cudaGraphCreate(&b->graph, 0);
+  cudaGraphNode_t prev = nullptr;
+  int swaps[2] = {0, 1};
+  void *argp = b->args_dev;
+  void *itemp = b->items_dev;
+  for (int t = 0; t < kGraphSteps && e == cudaSuccess; ++t) {
+    void *kp[3] = {&argp, &itemp, &swaps[t & 1]};
+    cudaKernelNodeParams np;
+    memset(&np, 0, sizeof(np));
+    np.func = const_cast<void *>(b->kernel);
+    np.gridDim = dim3(b->nitems);
+    np.blockDim = dim3(32, b->tile_y);
+    np.sharedMemBytes = (unsigned)b->smem;
+    np.kernelParams = kp;
+    cudaGraphNode_t node;
+    e = cudaGraphAddKernelNode(&node, b->graph, prev ? &prev : nullptr, prev ? 1 : 0, &np);
+    prev = node;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (e != cudaSuccess) return fail(SC_ECUDA, "building the batch graph: %s", cudaGetErrorString(e));
+  return SC_OK;
+}
+}  // namespace
+
 size_t sc_batch_workspace_bytes(int32_t n, const sc_params *params) {
   if (batch_validate(n, params) != SC_OK) return 0;
   size_t total = 0;
@@ -863,12 +972,6 @@ sc_status sc_batch_create(int32_t n, const sc_params *params, const double *cons
   const int storage = params[0].storage;
   const size_t arg_size = storage == SC_STORE_F64 ? sizeof(StepArgs<double>) : sizeof(StepArgs<float>);
   std::string host_args(arg_size * n, '\0');
-  int4 *items = new (std::nothrow) int4[nitems];
-  if (!items) {
-    sc_batch_destroy(b);
-    return fail(SC_ENOMEM, "host allocation failed");
-  }
-  int m = 0;
   for (int k = 0; k < n; ++k) {
     sc_ctx *c = b->ctx[k];
     if (storage == SC_STORE_F64) {
@@ -878,25 +981,28 @@ sc_status sc_batch_create(int32_t n, const sc_params *params, const double *cons
       StepArgs<float> a = step_args<float>(c);
       memcpy(&host_args[arg_size * k], &a, arg_size);
     }
-    const int gx = (c->p.nx + 31) / 32, gy = (c->p.ny + c->tile_y - 1) / c->tile_y,
-              gz = (c->p.nz + c->tile_z - 1) / c->tile_z;
-    for (int z = 0; z < gz; ++z)
-      for (int y = 0; y < gy; ++y)
-        for (int x = 0; x < gx; ++x)
-          if (m < nitems) items[m++] = make_int4(k, x, y, z);
-  }
-  if (m != nitems) {
-    delete[] items;
-    sc_batch_destroy(b);
-    return fail(SC_EINVAL, "batch work list size mismatch (%d vs %d)", m, nitems);
   }
   cudaError_t e = cudaMemcpyAsync(b->args_dev, host_args.data(), arg_size * n, cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(b->items_dev, items, sizeof(int4) * nitems, cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-  delete[] items;
   if (e != cudaSuccess) {
     sc_batch_destroy(b);
     return fail(SC_ECUDA, "uploading batch tables: %s", cudaGetErrorString(e));
+  }
+  b->retired = new (std::nothrow) char[n];
+  if (!b->retired) {
+    sc_batch_destroy(b);
+    return fail(SC_ENOMEM, "host allocation failed");
+  }
+  memset(b->retired, 0, n);
+  b->active = n;
+  st = batch_upload_items(b);
+  if (st != SC_OK) {
+    sc_batch_destroy(b);
+    return st;
+  }
+  if (b->nitems != nitems) {
+    sc_batch_destroy(b);
+    return fail(SC_EINVAL, "batch work list size mismatch (%d vs %d)", b->nitems, nitems);
   }
   const int lat = params[0].lattice == SC_D3Q19 ? kD3Q19 : kD2Q9;
   const int sten = params[0].stencil == SC_FORCE_E6 ? kE6 : kE4;
@@ -923,29 +1029,10 @@ sc_status sc_batch_create(int32_t n, const sc_params *params, const double *cons
     sc_batch_destroy(b);
     return fail(SC_EUNSUPPORTED, "no batched kernel for this lattice / stencil / tile_y / stages / blocks_per_sm");
   }
-  // a graph of kGraphSteps chained launches, swap = 0, 1, 0, 1, ...
-  e = cudaGraphCreate(&b->graph, 0);
-  cudaGraphNode_t prev = nullptr;
-  int swaps[2] = {0, 1};
-  void *argp = b->args_dev;
-  void *itemp = b->items_dev;
-  for (int t = 0; t < kGraphSteps && e == cudaSuccess; ++t) {
-    void *kp[3] = {&argp, &itemp, &swaps[t & 1]};
-    cudaKernelNodeParams np;
-    memset(&np, 0, sizeof(np));
-    np.func = const_cast<void *>(b->kernel);
-    np.gridDim = dim3(nitems);
-    np.blockDim = dim3(32, b->tile_y);
-    np.sharedMemBytes = (unsigned)b->smem;
-    np.kernelParams = kp;
-    cudaGraphNode_t node;
-    e = cudaGraphAddKernelNode(&node, b->graph, prev ? &prev : nullptr, prev ? 1 : 0, &np);
-    prev = node;
-  }
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
-  if (e != cudaSuccess) {
+  st = batch_build_graph(b);
+  if (st != SC_OK) {
     sc_batch_destroy(b);
-    return fail(SC_ECUDA, "building the batch graph: %s", cudaGetErrorString(e));
+    return st;
   }
   *out = b;
   return SC_OK;
@@ -954,6 +1041,7 @@ sc_status sc_batch_create(int32_t n, const sc_params *params, const double *cons
 sc_status sc_batch_step(sc_batch *b, int64_t nsteps) {
   if (!b) return fail(SC_EINVAL, "batch is NULL");
   if (nsteps < 0) return fail(SC_EINVAL, "nsteps must be >= 0");
+  if (b->nitems == 0) return SC_OK;  // every member retired
   auto single = [&]() -> cudaError_t {
     void *argp = b->args_dev;
     void *itemp = b->items_dev;
@@ -978,12 +1066,27 @@ sc_status sc_batch_step(sc_batch *b, int64_t nsteps) {
     if (e != cudaSuccess) return fail(SC_ECUDA, "batched step: %s", cudaGetErrorString(e));
   }
   for (int k = 0; k < b->n; ++k) {
+    if (b->retired[k]) continue;
     b->ctx[k]->cur = (int)(b->steps & 1);
     b->ctx[k]->steps = b->steps;
     b->ctx[k]->launches = b->launches;
   }
   return SC_OK;
 }
+
+sc_status sc_batch_retire(sc_batch *b, int32_t k) {
+  if (!b) return fail(SC_EINVAL, "batch is NULL");
+  if (k < 0 || k >= b->n) return fail(SC_EINVAL, "no batch member %d", k);
+  if (b->retired[k]) return SC_OK;
+  SC_CUDA(cudaStreamSynchronize(b->stream));
+  b->retired[k] = 1;
+  b->active -= 1;
+  sc_status st = batch_upload_items(b);
+  if (st == SC_OK) st = batch_build_graph(b);
+  return st;
+}
+
+int32_t sc_batch_active(const sc_batch *b) { return b ? b->active : 0; }
 
 sc_ctx *sc_batch_member(sc_batch *b, int32_t k) {
   if (!b || k < 0 || k >= b->n) {
@@ -1003,6 +1106,7 @@ void sc_batch_destroy(sc_batch *b) {
   if (b->ctx)
     for (int k = 0; k < b->n; ++k) delete b->ctx[k];
   delete[] b->ctx;
+  delete[] b->retired;
   delete b;
 }
 

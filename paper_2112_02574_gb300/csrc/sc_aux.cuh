@@ -187,29 +187,114 @@ __device__ __forceinline__ void force64(const ForceParams &p, const double *fiel
 
 // Common velocity of Eq. u (force included), FP64 [3][N].
 template <int LAT, int STEN, class ST>
-__global__ void velocity_kernel(PopArgs a, ForceParams fp, const double *fields, double *u) {
+__device__ __forceinline__ void site_velocity(const PopArgs &a, const ForceParams &fp, const double *fields,
+                                              int64_t s, double u[3]) {
   using L = Lattice<LAT>;
   const ST *buf = static_cast<const ST *>(a.buf);
   const int64_t N = a.N;
+  int x, y, z;
+  coords(s, a.nx, a.ny, x, y, z);
+  double F[2][3];
+  force64<LAT, STEN>(fp, fields, x, y, z, s, F);
+  double j[2][3] = {{0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+  for (int J = 0; J < 2; ++J)
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      const int64_t bwd = site_at(x - L::c(i, 0), y - L::c(i, 1), z - L::c(i, 2), a.nx, a.ny, a.nz);
+      const double g = pop_value<LAT, ST>(a, buf, i, J, bwd);
+#pragma unroll
+      for (int m = 0; m < 3; ++m) j[J][m] += L::c(i, m) * g;
+    }
+  const double n = fields[s] + fields[N + s];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) u[m] = ((j[0][m] + 0.5 * F[0][m]) + (j[1][m] + 0.5 * F[1][m])) / n;
+}
+
+template <int LAT, int STEN, class ST>
+__global__ void velocity_kernel(PopArgs a, ForceParams fp, const double *fields, double *u) {
+  const int64_t N = a.N;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+    double v[3];
+    site_velocity<LAT, STEN, ST>(a, fp, fields, s, v);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) u[m * N + s] = v[m];
+  }
+}
+
+// Convergence measure of section 4 (criterion on the velocity field): per-block
+// partial sums of sum_alpha |u_alpha(x) - u_prev_alpha(x)| over the sites (fixed
+// grid-stride order, fixed tree); u_prev is overwritten with u.
+template <int LAT, int STEN, class ST>
+__global__ void __launch_bounds__(256) velocity_change_partial_kernel(PopArgs a, ForceParams fp, const double *fields,
+                                                                      double *u_prev, double *partial) {
+  const int64_t N = a.N;
+  double acc = 0.0;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+    double v[3];
+    site_velocity<LAT, STEN, ST>(a, fp, fields, s, v);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      acc += fabs(v[m] - u_prev[m * N + s]);
+      u_prev[m * N + s] = v[m];
+    }
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+// Centre of mass of one density field's excess over a background value, partial
+// sums (w x, w y, w z, w) with w = n(x) - background, in lattice coordinates.
+__global__ void __launch_bounds__(256) com_partial_kernel(const double *n, int nx, int ny, int64_t N, double bg,
+                                                          double *partial) {
+  double acc[4] = {0, 0, 0, 0};
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
     int x, y, z;
-    coords(s, a.nx, a.ny, x, y, z);
-    double F[2][3];
-    force64<LAT, STEN>(fp, fields, x, y, z, s, F);
-    double j[2][3] = {{0, 0, 0}, {0, 0, 0}};
-#pragma unroll
-    for (int J = 0; J < 2; ++J)
-#pragma unroll
-      for (int i = 0; i < L::Q; ++i) {
-        const int64_t bwd = site_at(x - L::c(i, 0), y - L::c(i, 1), z - L::c(i, 2), a.nx, a.ny, a.nz);
-        const double g = pop_value<LAT, ST>(a, buf, i, J, bwd);
-#pragma unroll
-        for (int m = 0; m < 3; ++m) j[J][m] += L::c(i, m) * g;
-      }
-    const double n = fields[s] + fields[N + s];
-#pragma unroll
-    for (int m = 0; m < 3; ++m) u[m * N + s] = ((j[0][m] + 0.5 * F[0][m]) + (j[1][m] + 0.5 * F[1][m])) / n;
+    coords(s, nx, ny, x, y, z);
+    const double w = n[s] - bg;
+    acc[0] += w * x;
+    acc[1] += w * y;
+    acc[2] += w * z;
+    acc[3] += w;
   }
+  __shared__ double red[4][256];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) partial[blockIdx.x * 4 + c] = red[c][0];
+}
+
+// Block-order finalisation of the two reductions above: kind 0 -> out[0] = scale * sum;
+// kind 1 -> out = (X, Y, Z, M) with M the summed weight and X = sum w x / M.
+__global__ void finalize_measure_kernel(const double *partial, int nblocks, int kind, double scale, double *out) {
+  if (threadIdx.x != 0) return;
+  if (kind == 0) {
+    double acc = 0.0;
+    for (int k = 0; k < nblocks; ++k) acc += partial[k];
+    out[0] = scale * acc;
+    return;
+  }
+  double acc[4] = {0, 0, 0, 0};
+  for (int k = 0; k < nblocks; ++k)
+    for (int c = 0; c < 4; ++c) acc[c] += partial[k * 4 + c];
+  out[0] = acc[0] / acc[3];
+  out[1] = acc[1] / acc[3];
+  out[2] = acc[2] / acc[3];
+  out[3] = acc[3];
 }
 
 // Lattice pressure tensor of Eq. sm:pt at one site; P = {xx, yy, zz, xy, xz, yz}.

@@ -42,29 +42,86 @@ def droplet_sweep(radii, signs, make_fields, params_kw, steps: int, check_every:
     return sweep(members, steps, check_every, bin_width, device)
 
 
-def sweep(members, steps: int, check_every: int = 2048, bin_width=0.5, device="cuda"):
+def sweep(members, steps: int, check_every: int = 2048, bin_width=0.5, device="cuda", converge: bool = False,
+          dp_tol: float = 1e-5, du_tol: float = 1e-12):
     """Step the droplets described by `members` as one batch and return, per member, a dict with its side
-    L, sign (+1: A-rich, -1: B-rich), R and tag, and from the device: dP, R_s, sigma_s, P_in, P_out, and
-    dP_change = |dP(steps) - dP(steps - check_every)| / dP(steps - check_every) (the convergence measure
-    of section 4).  Each member is a dict with L (cube side), R, sign, params (make_params keywords),
-    fields ((n_A, n_B) initial densities) and optionally tag."""
+    L, sign (+1: A-rich, -1: B-rich), R and tag, and from the device: dP, R_s, sigma_s, P_in, P_out,
+    dP_change = |dP(t) - dP(t - check_every)| / dP(t - check_every), steps (run), converged, and
+    com_offset (largest coordinate distance of the droplet component's centre of mass from the centre
+    node).  Each member is a dict with L (cube side), R, sign, params (make_params keywords), fields
+    ((n_A, n_B) initial densities) and optionally tag.
+
+    converge=False: every member runs `steps` steps.  converge=True: section 4's criteria are checked
+    every check_every (= 2^11) steps -- a member has converged when the relative change of dP is below
+    dp_tol or the velocity change dU below du_tol -- and converged members are retired from the batch;
+    the rest run to `steps` at most."""
     plist = [B.make_params((m["L"],) * 3, **m["params"]) for m in members]
     batch = B.Batch(plist, [m["fields"] for m in members], device=device)
-    first = max(0, steps - check_every)
-    batch.step(first)
-    before = _analyse(batch, [m["L"] for m in members], bin_width)
-    batch.step(steps - first)
-    after = _analyse(batch, [m["L"] for m in members], bin_width)
+    n = len(members)
+    ran = [0] * n
+    done = [False] * n
+    change = [float("nan")] * n
+    if not converge:
+        first = max(0, steps - check_every)
+        batch.step(first)
+        before = _pressure_jumps(batch, [m["L"] for m in members]).cpu().numpy()
+        batch.step(steps - first)
+        after = _pressure_jumps(batch, [m["L"] for m in members]).cpu().numpy()
+        for k in range(n):
+            ran[k] = steps
+            change[k] = float(abs(after[k] - before[k]) / abs(before[k])) if before[k] != 0 else float("nan")
+    else:
+        u_prev = [m.moments()[2].clone() for m in batch.members]
+        prev = None
+        t = 0
+        while t < steps and batch.active > 0:
+            w = min(check_every, steps - t)
+            batch.step(w)
+            t += w
+            live = [k for k in range(n) if not done[k]]
+            dps = _pressure_jumps(batch, [members[k]["L"] for k in live], live)
+            dus = torch.cat([batch.members[k].velocity_change(u_prev[k]) for k in live])
+            dps, dus = dps.cpu().numpy(), dus.cpu().numpy()
+            for j, k in enumerate(live):
+                ran[k] = t
+                if prev is not None and prev[k] != 0:
+                    change[k] = float(abs(dps[j] - prev[k]) / abs(prev[k]))
+                if change[k] < dp_tol or dus[j] < du_tol:
+                    done[k] = True
+                    batch.retire(k)
+            prev = {k: dps[j] for j, k in enumerate(live)}
     for m in batch.members:
         B.sc_sync(m.ctx)  # raises on a non-finite or non-positive density
-    before, after = before.cpu().numpy(), after.cpu().numpy()
+    final = _analyse(batch, [m["L"] for m in members], bin_width).cpu().numpy()
     out = []
     for k, m in enumerate(members):
-        o, p = after[k], before[k]
+        o = final[k]
         out.append({"L": m["L"], "sign": m["sign"], "R": m["R"], "tag": m.get("tag"), "dP": float(o[0]),
                     "R_s": float(o[2]), "sigma_s": float(o[3]), "P_in": float(o[6]), "P_out": float(o[7]),
-                    "dP_change": float(abs(o[0] - p[0]) / abs(p[0])) if p[0] != 0 else float("nan")})
+                    "dP_change": change[k], "steps": ran[k], "converged": done[k] if converge else None,
+                    "com_offset": _com_offset(batch.members[k], m["L"], m["sign"])})
     return out
+
+
+def _pressure_jumps(batch, sides, which=None):
+    """P(centre node) - P(far corner) (Eq. bulkp, section 4) of the members `which` (all by default)."""
+    which = range(len(sides)) if which is None else which
+    out = []
+    for k, L in zip(which, sides):
+        m = batch.members[k]
+        out.append(m.bulk_pressure((L // 2,) * 3) - m.bulk_pressure((L - 1,) * 3))
+    return torch.cat(out)
+
+
+def _com_offset(member, L, sign):
+    """Largest coordinate distance between the centre node and the centre of mass of the droplet's
+    component (A for an A-rich droplet), counted above its density at the far corner (section 4 accepts
+    a run when this is below 1e-3)."""
+    comp = 0 if sign > 0 else 1
+    n = member.moments(with_u=False)[comp]
+    bg = float(n[L * L * L - 1].item())
+    c = member.centre_of_mass(comp, bg).cpu().numpy()
+    return float(max(abs(c[i] - L // 2) for i in range(3)))
 
 
 def _analyse(batch, sides, bin_width):
