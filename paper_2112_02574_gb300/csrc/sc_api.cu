@@ -77,22 +77,19 @@ int default_tile_y(const sc_params *p) {
   if (use_staged(p)) return staged_default_tile_y(p);
   return p->lattice == SC_D3Q19 ? 8 : 4;
 }
-// F32 with a self coupling (the psi ring and the self term make the block heavier):
-// one stage and three resident blocks per SM beat two stages and two blocks at every
-// size measured (128^3 .. 512^3); without one, two stages and two blocks.
+// F32 tile 32 x 4: one stage and three resident blocks per SM beat two stages and two
+// blocks, with and without a self coupling (128^3 .. 512^3, same-box comparisons);
+// F64 keeps two stages (three of its blocks do not fit in registers).
 bool has_self(const sc_params *p) { return p->G_self[0] != 0.0 || p->G_self[1] != 0.0; }
-bool f32_self_config(const sc_params *p, int tile_y) {
-  return p->storage == SC_STORE_F32 && tile_y == 4 && has_self(p);
-}
 int effective_stages(const sc_params *p, int tile_y) {
   if (p->stages) return p->stages;
-  if (f32_self_config(p, tile_y)) return 1;
-  return tile_y == 4 ? 2 : 1;
+  if (tile_y == 4) return p->storage == SC_STORE_F64 ? 2 : 1;
+  return 1;
 }
 int effective_blocks_per_sm(const sc_params *p, int tile_y) {
   if (p->blocks_per_sm) return p->blocks_per_sm;
-  if (f32_self_config(p, tile_y)) return 3;
-  return tile_y == 16 ? 1 : (tile_y == 8 ? 2 : (is_16bit(p->storage) ? 3 : 2));
+  if (tile_y == 4) return p->storage == SC_STORE_F64 ? 2 : 3;
+  return tile_y == 16 ? 1 : 2;
 }
 int default_tile_z(const sc_params *p) {
   if (p->lattice == SC_D2Q9) return 1;
@@ -799,18 +796,13 @@ bool batch_staged(int32_t n, const sc_params *params) {
 }
 // Member k's parameters as the batch steps it: the kernel variant of the batch and,
 // where the member leaves them to the library, stages and blocks_per_sm resolved
-// once for the whole batch (a self coupling in any member chooses the self-coupling
-// configuration for all, since every member runs in the same launch).
+// once for the whole batch from its first member (every member runs in the same launch).
 sc_params member_params(int32_t n, const sc_params *params, int k, bool staged) {
+  (void)n;
   sc_params q = params[k];
   q.variant = staged ? 2 : 1;
   sc_params rep = params[0];
   rep.variant = q.variant;
-  for (int j = 0; j < n; ++j)
-    if (has_self(&params[j])) {
-      rep.G_self[0] = params[j].G_self[0];
-      rep.G_self[1] = params[j].G_self[1];
-    }
   rep.stages = 0;
   rep.blocks_per_sm = 0;
   const int ty = default_tile_y(&q);

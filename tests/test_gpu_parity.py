@@ -161,9 +161,9 @@ def test_staged_kernel_equals_generic_bitwise(B, storage):
 @pytest.mark.parametrize("G_self", [(-0.4, 0.0), (0.0, 0.0)])
 def test_balanced_z_split_equals_generic(B, storage, G_self):
     """A box whose balanced split gives columns of unequal chunk counts (on a
-    152-SM GPU: FP32 without a self coupling 304 blocks over 30 columns, K = 10
-    with 4 columns of 11 chunks; FP32 with one, three blocks per SM, 456 blocks,
-    K = 15 with 6 columns of 16; FP16 304 blocks over 15 columns, K = 20):
+    152-SM GPU: FP32, three blocks per SM, 456 blocks over 30 columns, K = 15
+    with 6 columns of 16 chunks; FP16 304 blocks over 15 columns, K = 20 with 4
+    columns of 21):
     same state as the generic kernel, bit for bit; with and without a self
     coupling (without one the staged launch leaves the psi ring out)."""
     st = getattr(B, f"SC_STORE_{storage}")
