@@ -542,6 +542,106 @@ def precision_study(args, dev):
     print(json.dumps(out), flush=True)
 
 
+# The workload configurations (synthetic stand-ins, section 4 shapes): name -> setup
+STUDY_CONFIGS = {
+    "1 D2Q9 64^2": dict(shape=(64, 64, 1), lattice="d2q9", stencil="e4", psi="n", G=4.2, G_self=(0.0, 0.0),
+                        init=("droplet", 12.0), gpu_steps=2000, storages=("f32",), orc=(400, 100)),
+    "2 D3Q19 128^3": dict(shape=(128, 128, 128), lattice="d3q19", stencil="e4", psi="exp", G=3.6,
+                          G_self=(0.0, 0.0), init=("droplet", 24.0), gpu_steps=2048,
+                          storages=("f32", "f16", "bf16"), orc=(6, 2)),
+    "3 slab 64x64x256 E6": dict(shape=(64, 64, 256), lattice="d3q19", stencil="e6", psi="exp", G=3.6,
+                                G_self=(-0.6, 0.0), init=("slab", 128.0), gpu_steps=1024, storages=("f32",),
+                                orc=(4, 1)),
+    "5 D3Q19 512^3": dict(shape=(512, 512, 512), lattice="d3q19", stencil="e4", psi="exp", G=3.6,
+                          G_self=(-0.6, 0.0), init=("droplet", 96.0), gpu_steps=64,
+                          storages=("f32", "f16", "bf16"), orc=(1, 1), orc_shape=(256, 256, 256)),
+}
+
+
+def _config_fields(cfg, shape):
+    import sc_synth
+
+    kind, size = cfg["init"]
+    if kind == "slab":
+        return sc_synth.slab(shape[::-1], size, amplitude=1e-3)
+    R = size * shape[0] / cfg["shape"][0]
+    return sc_synth.droplet(shape[::-1], tuple(n // 2 for n in shape), R, n_in=0.95, n_out=0.05, amplitude=1e-3)
+
+
+def _oracle_rate(name, steps, q=None):
+    """MLUPS of the FP64 oracle on configuration `name` (at its oracle shape) over `steps` steps."""
+    import oracle
+
+    cfg = STUDY_CONFIGS[name]
+    shape = cfg.get("orc_shape", cfg["shape"])
+    op = oracle.Params(shape=shape, lattice=oracle.D3Q19 if cfg["lattice"] == "d3q19" else oracle.D2Q9,
+                       stencil=1 if cfg["stencil"] == "e6" else 0,
+                       psi_self=oracle.PSI_EXP if cfg["psi"] == "exp" else oracle.PSI_N, G=cfg["G"],
+                       G_self=cfg["G_self"])
+    f = oracle.init(op, *_config_fields(cfg, shape))
+    t0 = time.perf_counter()
+    f = oracle.step(op, f, steps)
+    dt = time.perf_counter() - t0
+    res = {"MLUPS": shape[0] * shape[1] * shape[2] * steps / dt / 1e6, "threads": oracle.threads(),
+           "shape": list(shape), "steps": steps, "seconds": dt}
+    if q is not None:
+        q.put(res)
+    return res
+
+
+def _oracle_one_thread(name, steps, q):
+    os.environ["OMP_NUM_THREADS"] = "1"
+    _oracle_rate(name, steps, q)
+
+
+def configs_study(args, dev):
+    """Each workload configuration: the GPU step rate (CUDA events, fused steps only) in its storage modes,
+    and the FP64 oracle's rate on the host cores (all threads, and one thread in a spawned process)."""
+    import multiprocessing as mp
+
+    import torch
+
+    from paper_2112_02574_gb300 import binding as B
+
+    codes = {"f32": B.SC_STORE_F32, "f16": B.SC_STORE_F16, "bf16": B.SC_STORE_BF16}
+    out = {"study": "workload configurations: GPU step rate and FP64 oracle rate", "configs": {}}
+    ctx = mp.get_context("spawn")
+    for name, cfg in STUDY_CONFIGS.items():
+        res = {"shape": list(cfg["shape"]), "gpu": {}}
+        # the oracle first: one thread in a spawned child, then all threads here
+        q = ctx.Queue()
+        pr = ctx.Process(target=_oracle_one_thread, args=(name, cfg["orc"][1], q))
+        pr.start()
+        res["oracle_1_thread"] = q.get()
+        pr.join()
+        res["oracle_all_threads"] = _oracle_rate(name, cfg["orc"][0])
+        shape = cfg["shape"]
+        nA, nB = _config_fields(cfg, shape)
+        for st in cfg["storages"]:
+            p = B.make_params(shape, lattice=B.SC_D3Q19 if cfg["lattice"] == "d3q19" else B.SC_D2Q9,
+                              stencil=B.SC_FORCE_E6 if cfg["stencil"] == "e6" else B.SC_FORCE_E4,
+                              psi_self=B.SC_PSI_EXP if cfg["psi"] == "exp" else B.SC_PSI_N, storage=codes[st],
+                              G=cfg["G"], G_self=cfg["G_self"])
+            sim = B.Simulation(p, nA, nB, device=dev)
+            sim.step(max(8, cfg["gpu_steps"] // 8))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(sim.stream)
+            sim.step(cfg["gpu_steps"])
+            b.record(sim.stream)
+            b.synchronize()
+            sim.sync()
+            ms = a.elapsed_time(b) / cfg["gpu_steps"]
+            sites = shape[0] * shape[1] * shape[2]
+            res["gpu"][st] = {"MLUPS": sites / (ms * 1e-3) / 1e6, "us_per_step": ms * 1e3,
+                              "hbm_frac": sites * BYTES_PER_SITE[st] / (ms * 1e-3) / 1e9 / measured_peak()[0],
+                              "launch": sim.step_config}
+            del sim
+            torch.cuda.empty_cache()
+        out["configs"][name] = res
+        print(json.dumps({name: res}), flush=True)
+    print(json.dumps(out), flush=True)
+
+
 PAPER_SIDES = (25, 31, 37, 41, 51, 57, 65)  # section 4's system sizes up to 65; R = L / 4
 PAPER_DGAB = (0.0, 0.48, -0.48, 0.88, -0.88)
 
@@ -623,9 +723,10 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched radius sweep block")
     ap.add_argument("--inner", type=int, default=INNER, help="time steps per benchmark step (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--study", choices=["precision", "paper"],
+    ap.add_argument("--study", choices=["precision", "paper", "configs"],
                     help="run only a study (minutes) and print its JSON line: precision = every result in each "
-                         "storage against the FP64 path; paper = Tolman length on the couplings of Eq. self_p")
+                         "storage against the FP64 path; paper = Tolman length on the couplings of Eq. self_p; "
+                         "configs = GPU and oracle rates of every workload configuration")
     ap.add_argument("--study-storage", default="f32", choices=["f64", "f32", "f16", "bf16"])
     ap.add_argument("--study-density", type=float, default=2.0, help="total density of the paper study")
     ap.add_argument("--study-steps", type=int, default=16384, help="time steps of the Tolman sweep and slab")
@@ -641,7 +742,8 @@ def main():
         return
     if args.study:
         if rank == 0:
-            (precision_study if args.study == "precision" else paper_tolman_study)(args, "cuda")
+            {"precision": precision_study, "paper": paper_tolman_study, "configs": configs_study}[args.study](
+                args, "cuda")
         return
     if world > 1:
         import torch

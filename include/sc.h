@@ -84,7 +84,8 @@ typedef struct {
   int32_t tile_z;      /* planes per step-kernel work item (>= 1); 0 = library default
                           (32; for the staged kernel on a lattice whose grid of 32-plane
                           chunks would fill fewer than four waves of the GPU, a balanced
-                          split whose grid fills whole waves) */
+                          split whose grid fills whole waves; for the generic D3Q19 kernel,
+                          8 .. 32 planes for about four blocks per SM) */
   int32_t variant;     /* step kernel: 0 = automatic, 1 = generic (any size, any stencil),
                           2 = cp.async-staged (D3Q19, E4, nx % 32 == 0, nx >= 64,
                           tile_y 4 or 8; tile_y 4 for F64); both compute the same numbers */
@@ -114,7 +115,10 @@ sc_status sc_create(const sc_params *params, const double *nA0, const double *nB
 
 /* Advance nsteps >= 0 time steps of Eq. lbm (BGK of Eq. omega_i, Guo forcing,
  * equilibrium of Eq. feq, common velocity of Eq. u, force of Eq. sc_force,
- * streaming).  One fused kernel launch per step; asynchronous. */
+ * streaming).  One fused kernel launch per step; asynchronous.  Runs of 32 steps
+ * are replayed from a CUDA graph of 32 launches that the context captures once,
+ * on a private stream, the first time such a run comes up (the replay goes to the
+ * context's stream; if the capture is not possible the steps are plain launches). */
 sc_status sc_step(sc_ctx *ctx, int64_t nsteps);
 
 /* Densities n_A, n_B (device FP64 [N] each) and, if u != NULL, the common

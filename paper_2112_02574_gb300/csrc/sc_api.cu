@@ -189,6 +189,13 @@ struct sc_ctx {
   int64_t steps;
   int64_t fields_at;  // step count the FP64 fields were computed at (-1: stale)
   int in_batch;       // stepped by a batch (sc_step refuses)
+  // kGraphSteps consecutive step launches from buffer 0, captured once on a private
+  // stream and replayed on the context's stream (graph_failed: capture not possible,
+  // plain launches only)
+  cudaStream_t cap_stream;
+  cudaGraph_t graph;
+  cudaGraphExec_t graph_exec;
+  int graph_failed;
 };
 
 struct sc_batch {
@@ -468,6 +475,18 @@ sc_status sc_create(const sc_params *params, const double *nA0, const double *nB
   c->stages = effective_stages(params, c->tile_y);
   c->blocks_per_sm = effective_blocks_per_sm(params, c->tile_y);
   c->fields_at = -1;
+  if (!c->staged && params->tile_z == 0 && params->lattice == SC_D3Q19) {
+    // generic kernel: z-chunks short enough for about four blocks per SM (a 64 x 64 x 256 box has
+    // only 16 columns), but at least 8 planes (each chunk re-sums 2 HALO z-halo planes)
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ==
+                                                  cudaSuccess && sms > 0) {
+      const int64_t cols = (int64_t)((params->nx + 31) / 32) * ((params->ny + c->tile_y - 1) / c->tile_y);
+      int64_t tz = cols * params->nz / (4 * (int64_t)sms);
+      tz = tz < 8 ? 8 : (tz > 32 ? 32 : tz);
+      c->tile_z = (int)(tz < params->nz ? tz : params->nz);
+    }
+  }
   if (c->staged && params->tile_z == 0) {
     st = plan_balanced_split(c);
     if (st != SC_OK) {
@@ -515,13 +534,67 @@ sc_status sc_create(const sc_params *params, const double *nA0, const double *nB
   return SC_OK;
 }
 
+namespace {
+constexpr int kStepGraphSteps = 32;  // steps per replay of a context's step graph (even: parity kept)
+
+// Capture kStepGraphSteps step launches (starting from buffer 0) on a private stream and
+// instantiate them.  Any failure leaves the context on plain launches (graph_failed).
+void build_step_graph(sc_ctx *c) {
+  cudaStream_t user = c->stream;
+  const int64_t launches = c->launches, steps = c->steps, fields_at = c->fields_at;
+  bool ok = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+  if (ok) {
+    c->stream = c->cap_stream;
+    ok = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+    if (ok) {
+      for (int t = 0; t < kStepGraphSteps && ok; ++t) ok = launch_one_step(c) == SC_OK;
+      cudaGraph_t g = nullptr;
+      const bool ended = cudaStreamEndCapture(c->cap_stream, &g) == cudaSuccess;
+      ok = ok && ended && g;
+      if (ok) {
+        c->graph = g;
+        ok = cudaGraphInstantiate(&c->graph_exec, g, 0) == cudaSuccess;
+      } else if (g) {
+        cudaGraphDestroy(g);
+      }
+    }
+  }
+  c->stream = user;
+  c->cur = 0;
+  c->launches = launches;
+  c->steps = steps;
+  c->fields_at = fields_at;
+  if (!ok) {
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+    c->graph = nullptr;
+    c->graph_failed = 1;
+    cudaGetLastError();  // the capture's error is not the caller's
+  }
+}
+}  // namespace
+
 sc_status sc_step(sc_ctx *c, int64_t nsteps) {
   if (!c) return fail(SC_EINVAL, "ctx is NULL");
   if (c->in_batch) return fail(SC_EINVAL, "this context belongs to a batch: step it with sc_batch_step");
   if (nsteps < 0) return fail(SC_EINVAL, "nsteps must be >= 0");
-  for (int64_t t = 0; t < nsteps; ++t) {
+  while (nsteps > 0) {
+    // runs of kStepGraphSteps from buffer 0 replay the step graph (built on first use,
+    // once the kernel has launched normally)
+    if (c->cur == 0 && nsteps >= kStepGraphSteps && c->launches >= 2 && !c->graph_failed) {
+      if (!c->graph_exec) build_step_graph(c);
+      if (c->graph_exec) {
+        SC_CUDA(cudaGraphLaunch(c->graph_exec, c->stream));
+        c->launches += kStepGraphSteps;
+        c->steps += kStepGraphSteps;
+        nsteps -= kStepGraphSteps;
+        continue;
+      }
+    }
     sc_status st = launch_one_step(c);
     if (st != SC_OK) return st;
+    nsteps -= 1;
   }
   return SC_OK;
 }
@@ -796,7 +869,8 @@ bool batch_staged(int32_t n, const sc_params *params) {
 }
 // Member k's parameters as the batch steps it: the kernel variant of the batch and,
 // where the member leaves them to the library, stages and blocks_per_sm resolved
-// once for the whole batch from its first member (every member runs in the same launch).
+// once for the whole batch from its first member (every member runs in the same launch)
+// and the plain tile_z chunking the batch's work list uses.
 sc_params member_params(int32_t n, const sc_params *params, int k, bool staged) {
   (void)n;
   sc_params q = params[k];
@@ -808,6 +882,7 @@ sc_params member_params(int32_t n, const sc_params *params, int k, bool staged) 
   const int ty = default_tile_y(&q);
   if (!q.stages) q.stages = effective_stages(&rep, ty);
   if (!q.blocks_per_sm) q.blocks_per_sm = effective_blocks_per_sm(&rep, ty);
+  if (!q.tile_z) q.tile_z = default_tile_z(&q);  // fixed chunks: the work list is built from them
   return q;
 }
 
@@ -1123,7 +1198,13 @@ sc_status sc_reference_density(const sc_ctx *c, double nbar[2]) {
   return SC_OK;
 }
 
-void sc_destroy(sc_ctx *c) { delete c; }
+void sc_destroy(sc_ctx *c) {
+  if (!c) return;
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  delete c;
+}
 
 const char *sc_last_error(void) { return g_err.c_str(); }
 

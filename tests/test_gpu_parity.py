@@ -410,3 +410,19 @@ def test_run_host_matches_device_path(B):
     nA, nB, _ = sim.moments(with_u=False)
     np.testing.assert_array_equal(oA.numpy(), nA.cpu().numpy())
     np.testing.assert_array_equal(oB.numpy(), nB.cpu().numpy())
+
+
+def test_step_graph_replay_equals_plain_launches(B):
+    """Runs of 32 steps replay a captured CUDA graph; stepping 1 + 70 + 3 steps (graph
+    replays and plain launches mixed, odd start parity included) gives the state of 74
+    plain single steps, bit for bit, and counts every step as a launch."""
+    shape = (64, 21, 19)
+    f = S.droplet(shape[::-1], (32, 10, 9), 4.0, n_in=0.85, n_out=0.15, amplitude=1e-3)
+    p = B.make_params(shape, psi_self=1, storage=B.SC_STORE_F32, G=2.5, G_self=(-0.4, 0.0))
+    a, b = B.Simulation(p, *f), B.Simulation(p, *f)
+    for n in (1, 70, 3):
+        a.step(n)
+    for _ in range(74):
+        b.step(1)
+    np.testing.assert_array_equal(a.state().cpu().numpy(), b.state().cpu().numpy())
+    assert a.launches == 74 and b.launches == 74
