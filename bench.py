@@ -542,17 +542,17 @@ def precision_study(args, dev):
     print(json.dumps(out), flush=True)
 
 
-# The workload configurations (synthetic stand-ins, section 4 shapes): name -> setup
+# The workloads (synthetic stand-ins with section 4's shapes): name -> setup
 STUDY_CONFIGS = {
-    "1 D2Q9 64^2": dict(shape=(64, 64, 1), lattice="d2q9", stencil="e4", psi="n", G=4.2, G_self=(0.0, 0.0),
+    "D2Q9 64^2 droplet": dict(shape=(64, 64, 1), lattice="d2q9", stencil="e4", psi="n", G=4.2, G_self=(0.0, 0.0),
                         init=("droplet", 12.0), gpu_steps=2000, storages=("f32",), orc=(400, 100)),
-    "2 D3Q19 128^3": dict(shape=(128, 128, 128), lattice="d3q19", stencil="e4", psi="exp", G=3.6,
+    "D3Q19 128^3 droplet": dict(shape=(128, 128, 128), lattice="d3q19", stencil="e4", psi="exp", G=3.6,
                           G_self=(0.0, 0.0), init=("droplet", 24.0), gpu_steps=2048,
                           storages=("f32", "f16", "bf16"), orc=(6, 2)),
-    "3 slab 64x64x256 E6": dict(shape=(64, 64, 256), lattice="d3q19", stencil="e6", psi="exp", G=3.6,
+    "D3Q19 64x64x256 slab, E6": dict(shape=(64, 64, 256), lattice="d3q19", stencil="e6", psi="exp", G=3.6,
                                 G_self=(-0.6, 0.0), init=("slab", 128.0), gpu_steps=1024, storages=("f32",),
                                 orc=(4, 1)),
-    "5 D3Q19 512^3": dict(shape=(512, 512, 512), lattice="d3q19", stencil="e4", psi="exp", G=3.6,
+    "D3Q19 512^3 droplet": dict(shape=(512, 512, 512), lattice="d3q19", stencil="e4", psi="exp", G=3.6,
                           G_self=(-0.6, 0.0), init=("droplet", 96.0), gpu_steps=64,
                           storages=("f32", "f16", "bf16"), orc=(1, 1), orc_shape=(256, 256, 256)),
 }

@@ -49,7 +49,7 @@ typedef enum {
                            psi = exp(-1/n) is in use (with psi = n the method stays defined
                            for transiently negative densities, and they are not flagged) */
   SC_ETIMEOUT = 5,      /* a bounded device-side wait ran out */
-  SC_EUNSUPPORTED = 6   /* valid request this build does not implement */
+  SC_EUNSUPPORTED = 6   /* valid request the library has no kernel for */
 } sc_status;
 
 typedef enum { SC_D2Q9 = 0, SC_D3Q19 = 1 } sc_lattice;
