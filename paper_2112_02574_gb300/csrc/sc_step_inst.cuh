@@ -2,22 +2,35 @@
 // (so the four instantiation sets compile in parallel).
 #pragma once
 
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "sc_dispatch.h"
 #include "sc_step_kernel.cuh"
 #include "sc_step_staged.cuh"
 
 namespace scgb {
 
+// Set a kernel's dynamic shared-memory limit once per device (the attribute belongs to
+// the function on the current device); false (with the CUDA error pending) on failure.
+inline bool attr_once(const void *k, size_t smem) {
+  static std::mutex m;
+  static std::set<std::pair<const void *, int>> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  std::lock_guard<std::mutex> lock(m);
+  if (done.count({k, dev})) return true;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) return false;
+  done.insert({k, dev});
+  return true;
+}
+
 template <int LAT, int STEN, class ST, class CT, int TY>
 cudaError_t launch_one(const StepLaunch &l, const StepArgs<CT> &a) {
   constexpr size_t smem = step_smem_bytes<LAT, STEN, CT, TY>();
   auto *k = sc_step_kernel<LAT, STEN, ST, CT, TY>;
-  static bool attr_set = false;  // the attribute is per function; set it once
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  if (!attr_once(reinterpret_cast<const void *>(k), smem)) return cudaGetLastError();
   k<<<l.grid, dim3(32, TY), smem, l.stream>>>(a);
   return cudaGetLastError();
 }
@@ -28,12 +41,7 @@ cudaError_t launch_staged_one(const StepLaunch &l, const StepArgs<CT> &a) {
   constexpr size_t smem_max = staged_smem_bytes<ST, CT, TY, NS>();
   const size_t smem = staged_smem_bytes<ST, CT, TY, NS>(a.self_on != 0);
   auto *k = sc_step_staged<ST, CT, TY, NS, MINB>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_max));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  if (!attr_once(reinterpret_cast<const void *>(k), smem_max)) return cudaGetLastError();
   const dim3 grid = a.zbal_k > 0 ? dim3(a.zbal_k * a.zbal_cols + a.zbal_rem)
                                  : dim3((a.nx + 31) / 32, (a.ny + TY - 1) / TY, (a.nz + a.tile_z - 1) / a.tile_z);
   k<<<grid, dim3(32, TY), smem, l.stream>>>(a);
