@@ -97,3 +97,23 @@ def test_batch_member_analysis_and_guard(B):
     with pytest.raises(B.ScError) as e:
         m.step(1)
     assert e.value.status == B.SC_EINVAL
+
+
+def test_staged_batch_fp64_member_matches_oracle(B):
+    """FP64 storage, sides 4 ceil(R) (the staged kernel, partial x tiles): a batch member
+    against the FP64 oracle, one step and twelve."""
+    sets = []
+    for k, R in enumerate((8.0, 9.0)):
+        L = 4 * int(np.ceil(R))
+        kw = dict(G=2.5, G_self=(0.0, 0.0) if k == 0 else (-0.4, 0.1), tau=(1.0, 0.9))
+        f = S.droplet((L, L, L), (L // 2,) * 3, R, n_in=0.85, n_out=0.15, amplitude=1e-3, seed=400 + k)
+        sets.append((B.make_params((L, L, L), lattice=B.SC_D3Q19, psi_self=B.SC_PSI_EXP, storage=B.SC_STORE_F64,
+                                   tile_z=8, **kw), f, kw, L))
+    batch = B.Batch([x[0] for x in sets], [x[1] for x in sets])
+    assert batch.staged
+    batch.step(12)
+    for (p, f, kw, L), m in zip(sets, batch.members):
+        op = oracle.Params(shape=(L, L, L), lattice=oracle.D3Q19, psi_self=oracle.PSI_EXP, **kw)
+        ref = oracle.step(op, oracle.init(op, *f), 12)
+        got = m.populations().cpu().numpy()
+        assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max()
