@@ -405,7 +405,7 @@ def sweep_droplets():
     return out
 
 
-BATCH_CANDIDATES = [(8, 32, 1, 2), (8, 16, 1, 2), (4, 32, 1, 3), (4, 16, 2, 3), (4, 32, 2, 2)]
+BATCH_CANDIDATES = [(8, 64, 1, 2), (4, 32, 1, 3), (4, 64, 1, 3), (4, 128, 1, 3), (4, 64, 2, 2)]
 
 
 def batch_block(B, dev, stream, plain_mlups, steps=128):

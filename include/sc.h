@@ -82,10 +82,10 @@ typedef struct {
   int32_t storage;     /* sc_storage */
   int32_t tile_y;      /* step-kernel tile rows (1, 2, 4 or 8); 0 = library default */
   int32_t tile_z;      /* planes per step-kernel work item (>= 1); 0 = library default
-                          (32; for the staged kernel on a lattice whose grid of 32-plane
-                          chunks would fill fewer than four waves of the GPU, a balanced
-                          split whose grid fills whole waves; for the generic D3Q19 kernel,
-                          8 .. 32 planes for about four blocks per SM) */
+                          (staged kernel: 128 or 64 planes where that grid fills eight
+                          waves of the GPU, else 32 where that fills four, else a balanced
+                          split whose grid fills whole waves; in a batch 64; generic D3Q19
+                          kernel: 8 .. 32 planes for about four blocks per SM; 32 otherwise) */
   int32_t variant;     /* step kernel: 0 = automatic, 1 = generic (any size, any stencil),
                           2 = cp.async-staged (D3Q19, E4, nx % 32 == 0, nx >= 64,
                           tile_y 4 or 8; tile_y 4 for F64); both compute the same numbers */
