@@ -680,8 +680,9 @@ def paper_tolman_study(args, dev):
             for sign in (1, -1):
                 inside = (fl["A_in"], fl["B_in"]) if sign > 0 else (fl["A_out"], fl["B_out"])
                 outside = (fl["A_out"], fl["B_out"]) if sign > 0 else (fl["A_in"], fl["B_in"])
+                # section 4's initial profile as printed: no noise (the slab pre-run keeps its +-1e-3)
                 f = sc_synth.droplet_ab((L, L, L), (L // 2,) * 3, L / 4.0, inside[0], outside[0], inside[1],
-                                        outside[1], amplitude=1e-3)
+                                        outside[1], amplitude=0.0)
                 members.append({"L": L, "R": L / 4.0, "sign": sign, "params": kw, "fields": f, "tag": d})
     t0 = time.perf_counter()
     drops = tolman.sweep(members, T, device=dev, converge=True)
