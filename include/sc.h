@@ -85,7 +85,7 @@ typedef struct {
                           (staged kernel: 128 or 64 planes where that grid fills eight
                           waves of the GPU, else 32 where that fills four, else a balanced
                           split whose grid fills whole waves; in a batch 64; generic D3Q19
-                          kernel: 8 .. 32 planes for about four blocks per SM; 32 otherwise) */
+                          kernel: 16 .. 32 planes for about two blocks per SM; 32 otherwise) */
   int32_t variant;     /* step kernel: 0 = automatic, 1 = generic (any size, any stencil),
                           2 = cp.async-staged (D3Q19, E4, nx % 32 == 0, nx >= 64,
                           tile_y 4 or 8; tile_y 4 for F64); both compute the same numbers */

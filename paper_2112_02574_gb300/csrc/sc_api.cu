@@ -485,14 +485,15 @@ sc_status sc_create(const sc_params *params, const double *nA0, const double *nB
   c->blocks_per_sm = effective_blocks_per_sm(params, c->tile_y);
   c->fields_at = -1;
   if (!c->staged && params->tile_z == 0 && params->lattice == SC_D3Q19) {
-    // generic kernel: z-chunks short enough for about four blocks per SM (a 64 x 64 x 256 box has
-    // only 16 columns), but at least 8 planes (each chunk re-sums 2 HALO z-halo planes)
+    // generic kernel: z-chunks short enough for about two blocks per SM (a 64 x 64 x 256 box has
+    // only 16 columns), but at least 16 planes, since each chunk re-sums 2 HALO z-halo planes
+    // (E6 slab 64 x 64 x 256: 16 planes 10.5 GLUPS, 8 planes 9.2, 32 planes 7.2)
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ==
                                                   cudaSuccess && sms > 0) {
       const int64_t cols = (int64_t)((params->nx + 31) / 32) * ((params->ny + c->tile_y - 1) / c->tile_y);
-      int64_t tz = cols * params->nz / (4 * (int64_t)sms);
-      tz = tz < 8 ? 8 : (tz > 32 ? 32 : tz);
+      int64_t tz = cols * params->nz / (2 * (int64_t)sms);
+      tz = tz < 16 ? 16 : (tz > 32 ? 32 : tz);
       c->tile_z = (int)(tz < params->nz ? tz : params->nz);
     }
   }
