@@ -80,18 +80,20 @@ typedef struct {
   int32_t stencil;     /* sc_stencil */
   int32_t psi_self;    /* sc_psi */
   int32_t storage;     /* sc_storage */
-  int32_t tile_y;      /* step-kernel tile rows (1, 2, 4 or 8); 0 = library default */
+  int32_t tile_y;      /* step-kernel tile rows (1, 2, 4 or 8; 16 staged only); 0 = library default */
   int32_t tile_z;      /* planes per step-kernel work item (>= 1); 0 = library default
-                          (staged kernel: 128 or 64 planes where that grid fills eight
-                          waves of the GPU, else 32 where that fills four, else a balanced
-                          split whose grid fills whole waves; in a batch 64; generic D3Q19
-                          kernel: 16 .. 32 planes for about two blocks per SM; 32 otherwise) */
-  int32_t variant;     /* step kernel: 0 = automatic, 1 = generic (any size, any stencil),
-                          2 = cp.async-staged (D3Q19, E4, nx % 32 == 0, nx >= 64,
-                          tile_y 4 or 8; tile_y 4 for F64); both compute the same numbers */
+                          (D3Q19: staged kernel 128 or 64 planes where that grid fills
+                          eight waves of the GPU; either kernel 32 where that fills four,
+                          else a balanced split whose grid fills whole waves; a batch: 64
+                          staged, 32 generic; D2Q9: 1) */
+  int32_t variant;     /* step kernel: 0 = automatic (staged where it can run), 1 = generic
+                          (any size, any stencil), 2 = cp.async-staged (D3Q19, E4, nx >= 32
+                          a multiple of the sites per 16-byte chunk: 1 F64, 2 F32, 4 F16 and
+                          BF16; tile_y 4, 8 or 16, F64 tile_y 4 only); both kernels compute
+                          the same numbers */
   int32_t stages;      /* staged kernel copy pipeline: 1 or 2 planes in flight; 0 = default */
   int32_t blocks_per_sm; /* staged kernel register budget: resident blocks per SM it must allow
-                          (tile_y 4: 2 or 3; tile_y 8: 1 or 2); 0 = default.  stages and
+                          (tile_y 4: 2 or 3; tile_y 8: 1 or 2; tile_y 16: 1); 0 = default.  stages and
                           blocks_per_sm change speed only, never the numbers */
   double tau[2];       /* tau_A, tau_B > 1/2 (Eq. omega_i) */
   double G;            /* inter-component coupling G */

@@ -327,42 +327,61 @@ StepArgs<CT> step_args(sc_ctx *c) {
   return a;
 }
 
-// z-chunking of the staged kernel when tile_z is left to the library: 128 or 64 planes
-// where that grid still fills eight waves of the GPU, 32 where a 32-plane grid fills four,
-// and otherwise a balanced z split: the grid is
-// exactly waves x (SMs x resident blocks per SM) blocks, with waves chosen for
-// z-chunks of about kTargetChunk planes (wave count rounded to nearest), and every column of 32 x tile_y sites is
-// cut into K or K + 1 equal z-chunks.  A fixed tile_z instead leaves a partly empty
-// last wave whenever the block count is not a multiple of the resident slots (at
-// 128^3: 256 blocks of 32 planes for 304 slots).
-sc_status plan_balanced_split(sc_ctx *c) {
-  constexpr int kTargetChunk = 18;  // 128^3 F32: 3 waves of 18-plane chunks beat 2 waves of 26 (+2 %)
+// Target z-chunk of the generic kernel's balanced split, in planes (same-box comparison, FP32
+// and FP16, E4 and E6: targets 16, 24 and 32 pick one full wave for the 64 x 64 x 256 slab and
+// 96^3, where all agree; at 128^3 two waves of 13-14 planes (target 16) beat one of 27 by 2 to
+// 9 %.  Against the earlier fixed 16..32-plane chunks: E6 slab 10.5 -> 11.4 GLUPS, E6 128^3
+// 8.2 -> 11.3, E6 96^3 8.9 -> 10.5).
+constexpr int kGenericTargetChunk = 16;
+
+// z-chunking of a D3Q19 lattice when tile_z is left to the library.  Staged kernel: 128 or
+// 64 planes where that grid still fills eight waves of the GPU.  Either kernel: 32 planes
+// where a 32-plane grid fills four waves, otherwise a balanced z split: the grid is exactly
+// waves x (SMs x resident blocks per SM) blocks, with waves chosen for z-chunks of about
+// a target chunk length (wave count rounded to nearest), and every column of 32 x tile_y sites
+// is cut into K or K + 1 equal z-chunks.  A fixed tile_z instead leaves a partly empty last
+// wave whenever the block count is not a multiple of the resident slots (staged, 128^3: 256
+// blocks of 32 planes for 304 slots; generic E6, 128^3: 320 blocks of 26 planes for 304).
+sc_status plan_z_split(sc_ctx *c) {
+  // staged 128^3 F32: 3 waves of 18-plane chunks beat 2 waves of 26 (+2 %); the generic
+  // kernel re-sums 2 HALO z-halo planes per chunk from L2 instead of a staged window
+  const int target_chunk = c->staged ? 18 : kGenericTargetChunk;
   int dev = 0, sms = 0, occ = 0;
   const bool self_on = has_self(&c->p);
+  const int lat = c->p.lattice == SC_D3Q19 ? kD3Q19 : kD2Q9, sten = c->p.stencil == SC_FORCE_E6 ? kE6 : kE4;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && c->staged) {
     switch (c->p.storage) {
       case SC_STORE_F32: e = staged_occupancy_f32(c->tile_y, c->stages, c->blocks_per_sm, self_on, &occ); break;
       case SC_STORE_F16: e = staged_occupancy_f16(c->tile_y, c->stages, c->blocks_per_sm, self_on, &occ); break;
       case SC_STORE_BF16: e = staged_occupancy_bf16(c->tile_y, c->stages, c->blocks_per_sm, self_on, &occ); break;
       default: e = staged_occupancy_f64(c->tile_y, c->stages, c->blocks_per_sm, self_on, &occ); break;
     }
+  } else if (e == cudaSuccess) {
+    switch (c->p.storage) {
+      case SC_STORE_F32: e = generic_occupancy_f32(lat, sten, c->tile_y, &occ); break;
+      case SC_STORE_F16: e = generic_occupancy_f16(lat, sten, c->tile_y, &occ); break;
+      case SC_STORE_BF16: e = generic_occupancy_bf16(lat, sten, c->tile_y, &occ); break;
+      default: e = generic_occupancy_f64(lat, sten, c->tile_y, &occ); break;
+    }
   }
-  if (e != cudaSuccess) return fail(SC_ECUDA, "occupancy of the staged kernel: %s", cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(SC_ECUDA, "occupancy of the step kernel: %s", cudaGetErrorString(e));
   const int64_t cols_x = (c->p.nx + 31) / 32, cols = cols_x * ((c->p.ny + c->tile_y - 1) / c->tile_y);
   const int64_t nz = c->p.nz, slots = (int64_t)sms * (occ > 0 ? occ : 1);
   // deep grids: the longest z-chunks (fewer re-summed z-halo planes per site) that still leave
   // eight waves (512^3: 16-bit +3.8 % with 128 planes over 32; 256^3 stays at 32)
-  for (int tz : {128, 64}) {
-    if (cols * ((nz + tz - 1) / tz) >= 8 * slots) {
-      c->tile_z = (int)(tz < nz ? tz : nz);
-      return SC_OK;
+  if (c->staged) {
+    for (int tz : {128, 64}) {
+      if (cols * ((nz + tz - 1) / tz) >= 8 * slots) {
+        c->tile_z = (int)(tz < nz ? tz : nz);
+        return SC_OK;
+      }
     }
   }
   const int64_t fixed_blocks = cols * ((nz + c->tile_z - 1) / c->tile_z);
   if (fixed_blocks >= 4 * slots) return SC_OK;  // many waves: the plain grid's last-wave loss is small
-  int64_t waves = (2 * cols * nz + slots * kTargetChunk) / (2 * slots * kTargetChunk);  // rounded
+  int64_t waves = (2 * cols * nz + slots * target_chunk) / (2 * slots * target_chunk);  // rounded
   if (waves < 1) waves = 1;
   int64_t G = slots * waves;
   const int64_t gmax = cols * (nz / 4 > 1 ? nz / 4 : 1);  // chunks of 4 planes or more
@@ -484,21 +503,8 @@ sc_status sc_create(const sc_params *params, const double *nA0, const double *nB
   c->stages = effective_stages(params, c->tile_y);
   c->blocks_per_sm = effective_blocks_per_sm(params, c->tile_y);
   c->fields_at = -1;
-  if (!c->staged && params->tile_z == 0 && params->lattice == SC_D3Q19) {
-    // generic kernel: z-chunks short enough for about two blocks per SM (a 64 x 64 x 256 box has
-    // only 16 columns), but at least 16 planes, since each chunk re-sums 2 HALO z-halo planes
-    // (E6 slab 64 x 64 x 256: 16 planes 10.5 GLUPS, 8 planes 9.2, 32 planes 7.2)
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ==
-                                                  cudaSuccess && sms > 0) {
-      const int64_t cols = (int64_t)((params->nx + 31) / 32) * ((params->ny + c->tile_y - 1) / c->tile_y);
-      int64_t tz = cols * params->nz / (2 * (int64_t)sms);
-      tz = tz < 16 ? 16 : (tz > 32 ? 32 : tz);
-      c->tile_z = (int)(tz < params->nz ? tz : params->nz);
-    }
-  }
-  if (c->staged && params->tile_z == 0) {
-    st = plan_balanced_split(c);
+  if (params->tile_z == 0 && params->lattice == SC_D3Q19) {
+    st = plan_z_split(c);
     if (st != SC_OK) {
       delete c;
       return st;

@@ -230,8 +230,8 @@ struct StepArgs {
   // n(s) - nbar is kept as an FP32 pair per site: read from nsrc, written to ndst.
   const float2 *nsrc;
   float2 *ndst;
-  // Balanced z split of the staged kernel (zbal_k > 0; 1-D grid of zbal_k * zbal_cols
-  // + zbal_rem blocks): zbal_cols = x tiles * y tiles, zbal_cols_x = x tiles.
+  // Balanced z split of a single-lattice step launch (zbal_k > 0; 1-D grid of
+  // zbal_k * zbal_cols + zbal_rem blocks): zbal_cols = x tiles * y tiles, zbal_cols_x = x tiles.
   int zbal_k, zbal_rem, zbal_cols, zbal_cols_x;
 };
 

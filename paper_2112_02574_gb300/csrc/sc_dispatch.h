@@ -14,7 +14,7 @@ struct StepLaunch {
   int staged;   // 1: cp.async-staged kernel (D3Q19, E4, nx >= 32, nx a multiple of the chunk sites)
   int stages;   // staged kernel: pipeline stages, 1 or 2
   int blocks_per_sm;  // staged kernel: resident blocks per SM its registers allow (tile_y 4: 2 or 3; 8: 1 or 2)
-  dim3 grid;    // generic kernel grid
+  dim3 grid;    // generic kernel grid without a balanced z split
   cudaStream_t stream;
 };
 
@@ -40,6 +40,12 @@ cudaError_t staged_occupancy_f32(int tile_y, int stages, int blocks_per_sm, bool
 cudaError_t staged_occupancy_f16(int tile_y, int stages, int blocks_per_sm, bool self_on, int *blocks);
 cudaError_t staged_occupancy_bf16(int tile_y, int stages, int blocks_per_sm, bool self_on, int *blocks);
 cudaError_t staged_occupancy_f64(int tile_y, int stages, int blocks_per_sm, bool self_on, int *blocks);
+
+// Resident blocks per SM of the generic step kernel for (lattice, stencil, tile_y).
+cudaError_t generic_occupancy_f32(int lattice, int stencil, int tile_y, int *blocks);
+cudaError_t generic_occupancy_f16(int lattice, int stencil, int tile_y, int *blocks);
+cudaError_t generic_occupancy_bf16(int lattice, int stencil, int tile_y, int *blocks);
+cudaError_t generic_occupancy_f64(int lattice, int stencil, int tile_y, int *blocks);
 
 // The batched staged step kernel (D3Q19, E4) for (tile_y, stages, blocks_per_sm),
 // same parameters and block shape as above; nullptr if not instantiated.  self_on:

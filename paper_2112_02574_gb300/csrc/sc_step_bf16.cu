@@ -13,3 +13,6 @@ const void *scgb::batched_staged_kernel_bf16(int tile_y, int stages, int blocks_
 cudaError_t scgb::staged_occupancy_bf16(int tile_y, int stages, int blocks_per_sm, bool self_on, int *blocks) {
   return staged_occupancy<__nv_bfloat16, float>(tile_y, stages, blocks_per_sm, self_on, blocks);
 }
+cudaError_t scgb::generic_occupancy_bf16(int lattice, int stencil, int tile_y, int *blocks) {
+  return generic_occupancy<__nv_bfloat16, float>(lattice, stencil, tile_y, blocks);
+}

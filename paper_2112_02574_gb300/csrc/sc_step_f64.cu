@@ -12,3 +12,6 @@ const void *scgb::batched_staged_kernel_f64(int tile_y, int stages, int blocks_p
 cudaError_t scgb::staged_occupancy_f64(int tile_y, int stages, int blocks_per_sm, bool self_on, int *blocks) {
   return staged_occupancy<double, double>(tile_y, stages, blocks_per_sm, self_on, blocks);
 }
+cudaError_t scgb::generic_occupancy_f64(int lattice, int stencil, int tile_y, int *blocks) {
+  return generic_occupancy<double, double>(lattice, stencil, tile_y, blocks);
+}

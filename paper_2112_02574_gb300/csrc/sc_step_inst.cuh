@@ -4,6 +4,7 @@
 
 #include <mutex>
 #include <set>
+#include <type_traits>
 #include <utility>
 
 #include "sc_dispatch.h"
@@ -31,8 +32,37 @@ cudaError_t launch_one(const StepLaunch &l, const StepArgs<CT> &a) {
   constexpr size_t smem = step_smem_bytes<LAT, STEN, CT, TY>();
   auto *k = sc_step_kernel<LAT, STEN, ST, CT, TY>;
   if (!attr_once(reinterpret_cast<const void *>(k), smem)) return cudaGetLastError();
-  k<<<l.grid, dim3(32, TY), smem, l.stream>>>(a);
+  const dim3 grid = a.zbal_k > 0 ? dim3(a.zbal_k * a.zbal_cols + a.zbal_rem) : l.grid;
+  k<<<grid, dim3(32, TY), smem, l.stream>>>(a);
   return cudaGetLastError();
+}
+
+template <int LAT, int STEN, class ST, class CT, int TY>
+cudaError_t generic_occupancy_one(int *blocks) {
+  constexpr size_t smem = step_smem_bytes<LAT, STEN, CT, TY>();
+  auto *k = sc_step_kernel<LAT, STEN, ST, CT, TY>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, 32 * TY, smem);
+}
+
+// Resident blocks per SM of the generic kernel for (lattice, stencil, tile_y).
+template <class ST, class CT>
+cudaError_t generic_occupancy(int lat, int sten, int ty, int *blocks) {
+  auto by_ty = [&](auto lat_c, auto sten_c) -> cudaError_t {
+    constexpr int LAT = decltype(lat_c)::value, STEN = decltype(sten_c)::value;
+    switch (ty) {
+      case 1: return generic_occupancy_one<LAT, STEN, ST, CT, 1>(blocks);
+      case 2: return generic_occupancy_one<LAT, STEN, ST, CT, 2>(blocks);
+      case 4: return generic_occupancy_one<LAT, STEN, ST, CT, 4>(blocks);
+      case 8: return generic_occupancy_one<LAT, STEN, ST, CT, 8>(blocks);
+      default: return cudaErrorInvalidValue;
+    }
+  };
+  if (lat == kD3Q19 && sten == kE4) return by_ty(std::integral_constant<int, kD3Q19>{}, std::integral_constant<int, kE4>{});
+  if (lat == kD3Q19 && sten == kE6) return by_ty(std::integral_constant<int, kD3Q19>{}, std::integral_constant<int, kE6>{});
+  if (lat == kD2Q9 && sten == kE4) return by_ty(std::integral_constant<int, kD2Q9>{}, std::integral_constant<int, kE4>{});
+  return cudaErrorInvalidValue;
 }
 
 // Staged kernel: one block per (x column, y column, z chunk), like the generic kernel.

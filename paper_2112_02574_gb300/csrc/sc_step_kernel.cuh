@@ -232,9 +232,40 @@ __device__ __forceinline__ void collide_site(const StepArgs<CT> &a, const P2<CT>
   }
 }
 
-// One block's work: the column (bx, by) x z-chunk bz of the lattice described by a.
+// The work of this block of a single-lattice launch: column (bx, by) of 32 x TY
+// sites, planes z0 .. zend - 1.  Balanced z split (a.zbal_k > 0; a 1-D grid of
+// K C + R blocks over the C = zbal_cols columns): chunk j of column c, columns c < R
+// cut into K + 1 equal z-chunks, the others into K, in chunk-major order.  Else the
+// 3-D grid of columns (blockIdx.x, blockIdx.y) and tile_z-plane chunks blockIdx.z.
+template <class CT>
+__device__ __forceinline__ void block_work(const StepArgs<CT> &a, int &bx, int &by, int &z0, int &zend) {
+  if (a.zbal_k > 0) {
+    const int b = blockIdx.x, C = a.zbal_cols, K = a.zbal_k;
+    int j, c;
+    if (b < K * C) {
+      j = b / C;
+      c = b - j * C;
+    } else {
+      j = K;
+      c = b - K * C;
+    }
+    const int kc = K + (c < a.zbal_rem ? 1 : 0);
+    z0 = (int)((int64_t)j * a.nz / kc);
+    zend = (int)((int64_t)(j + 1) * a.nz / kc);
+    by = c / a.zbal_cols_x;
+    bx = c - by * a.zbal_cols_x;
+  } else {
+    bx = blockIdx.x;
+    by = blockIdx.y;
+    z0 = blockIdx.z * a.tile_z;
+    zend = min(z0 + a.tile_z, a.nz);
+  }
+}
+
+// One block's work: the column (bx, by), planes z0 .. zend - 1, of the lattice described by a.
 template <int LAT, int STEN, class ST, class CT, int TY>
-__device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by, int bz, unsigned char *smem_raw) {
+__device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by, int z0, int zend,
+                                           unsigned char *smem_raw) {
   using L = Lattice<LAT>;
   using SN = Stencil<LAT, STEN>;
   constexpr int Q = L::Q;
@@ -253,8 +284,7 @@ __device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const int64_t N = a.N;
-  const int x0 = bx * 32, y0 = by * TY, z0 = bz * a.tile_z;
-  const int zend = min(z0 + a.tile_z, nz);
+  const int x0 = bx * 32, y0 = by * TY;
   const ST *__restrict__ src = static_cast<const ST *>(a.src);
   ST *__restrict__ dst = static_cast<ST *>(a.dst);
 
@@ -320,7 +350,9 @@ __device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by
 template <int LAT, int STEN, class ST, class CT, int TY>
 __global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 16 / TY)) sc_step_kernel(const StepArgs<CT> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  step_block<LAT, STEN, ST, CT, TY>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+  int bx, by, z0, zend;
+  block_work(a, bx, by, z0, zend);
+  step_block<LAT, STEN, ST, CT, TY>(a, bx, by, z0, zend, smem_raw);
 }
 
 // Batched form: one launch steps several lattices.  Block b works on item
@@ -340,7 +372,8 @@ __global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 16 / TY))
     a.nsrc = a.ndst;
     a.ndst = const_cast<float2 *>(u);
   }
-  step_block<LAT, STEN, ST, CT, TY>(a, it.y, it.z, it.w, smem_raw);
+  const int z0 = it.w * a.tile_z;
+  step_block<LAT, STEN, ST, CT, TY>(a, it.y, it.z, z0, min(z0 + a.tile_z, a.nz), smem_raw);
 }
 
 }  // namespace scgb

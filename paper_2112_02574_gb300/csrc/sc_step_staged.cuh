@@ -313,29 +313,7 @@ template <class ST, class CT, int TY, int NS, int MINB>
 __global__ void __launch_bounds__(32 * TY, MINB) sc_step_staged(const StepArgs<CT> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   int bx, by, z0, zend;
-  if (a.zbal_k > 0) {
-    // balanced split (1-D grid of K C + R blocks over C columns): chunk j of column c,
-    // columns c < R cut into K + 1 equal z-chunks, the others into K; chunk-major order
-    const int b = blockIdx.x, C = a.zbal_cols, K = a.zbal_k;
-    int j, c;
-    if (b < K * C) {
-      j = b / C;
-      c = b - j * C;
-    } else {
-      j = K;
-      c = b - K * C;
-    }
-    const int kc = K + (c < a.zbal_rem ? 1 : 0);
-    z0 = (int)((int64_t)j * a.nz / kc);
-    zend = (int)((int64_t)(j + 1) * a.nz / kc);
-    by = c / a.zbal_cols_x;
-    bx = c - by * a.zbal_cols_x;
-  } else {
-    bx = blockIdx.x;
-    by = blockIdx.y;
-    z0 = blockIdx.z * a.tile_z;
-    zend = min(z0 + a.tile_z, a.nz);
-  }
+  block_work(a, bx, by, z0, zend);
   staged_block<ST, CT, TY, NS>(a, bx, by, z0, zend, smem_raw);
 }
 

@@ -185,6 +185,32 @@ def test_balanced_z_split_equals_generic(B, storage, G_self):
     np.testing.assert_array_equal(outs[1], outs[0])
 
 
+@pytest.mark.parametrize("storage", ["F32", "F16", "F64"])
+@pytest.mark.parametrize("stencil", [0, 1])
+def test_generic_balanced_z_split_equals_fixed_chunks(B, storage, stencil):
+    """The generic kernel's balanced z split (1-D grid, columns cut into K or K + 1
+    chunks of unequal length) against fixed 5-plane chunks on a 3-D grid: the same
+    state bit for bit, E4 and E6 (a z reach of one and two planes)."""
+    import torch
+
+    st = getattr(B, f"SC_STORE_{storage}")
+    shape = (96, 40, 128)
+    f = S.droplet(shape[::-1], (48, 20, 64), 12.0, n_in=0.85, n_out=0.15, amplitude=1e-3)
+    outs = []
+    for tz in (5, 0):
+        sim = B.Simulation(B.make_params(shape, stencil=stencil, psi_self=1, storage=st, G=2.5, G_self=(-0.4, 0.1),
+                                         tile_z=tz, variant=1), *f)
+        sim.step(5)
+        sim.sync()
+        cfg = sim.step_config
+        assert cfg["variant"] == 1
+        if tz == 0:
+            sms = torch.cuda.get_device_properties(0).multi_processor_count
+            assert cfg["zsplit_k"] > 0 and cfg["blocks"] % sms == 0, cfg
+        outs.append(sim.state().cpu().numpy())
+    np.testing.assert_array_equal(outs[1], outs[0])
+
+
 @pytest.mark.parametrize("storage", ["F32", "F16", "BF16", "F64"])
 @pytest.mark.parametrize("nx", [32, 36, 44, 100])
 def test_staged_partial_x_tiles_equal_generic(B, storage, nx):
