@@ -607,14 +607,17 @@ def configs_study(args, dev):
     out = {"study": "workload configurations: GPU step rate and FP64 oracle rate", "configs": {}}
     ctx = mp.get_context("spawn")
     for name, cfg in STUDY_CONFIGS.items():
+        if args.study_config and args.study_config not in name:
+            continue
         res = {"shape": list(cfg["shape"]), "gpu": {}}
-        # the oracle first: one thread in a spawned child, then all threads here
-        q = ctx.Queue()
-        pr = ctx.Process(target=_oracle_one_thread, args=(name, cfg["orc"][1], q))
-        pr.start()
-        res["oracle_1_thread"] = q.get()
-        pr.join()
-        res["oracle_all_threads"] = _oracle_rate(name, cfg["orc"][0])
+        if not args.no_cpu_baseline:
+            # the oracle first: one thread in a spawned child, then all threads here
+            q = ctx.Queue()
+            pr = ctx.Process(target=_oracle_one_thread, args=(name, cfg["orc"][1], q))
+            pr.start()
+            res["oracle_1_thread"] = q.get()
+            pr.join()
+            res["oracle_all_threads"] = _oracle_rate(name, cfg["orc"][0])
         shape = cfg["shape"]
         nA, nB = _config_fields(cfg, shape)
         for st in cfg["storages"]:
@@ -728,6 +731,8 @@ def main():
                     help="run only a study (minutes) and print its JSON line: precision = every result in each "
                          "storage against the FP64 path; paper = Tolman length on the couplings of Eq. self_p; "
                          "configs = GPU and oracle rates of every workload configuration")
+    ap.add_argument("--study-config", default="",
+                    help="configs study: only the configurations whose name contains this text")
     ap.add_argument("--study-storage", default="f32", choices=["f64", "f32", "f16", "bf16"])
     ap.add_argument("--study-density", type=float, default=2.0, help="total density of the paper study")
     ap.add_argument("--study-steps", type=int, default=16384, help="time steps of the Tolman sweep and slab")

@@ -237,8 +237,16 @@ __device__ __forceinline__ void collide_site(const StepArgs<CT> &a, const P2<CT>
 // K C + R blocks over the C = zbal_cols columns): chunk j of column c, columns c < R
 // cut into K + 1 equal z-chunks, the others into K, in chunk-major order.  Else the
 // 3-D grid of columns (blockIdx.x, blockIdx.y) and tile_z-plane chunks blockIdx.z.
+// In the balanced split odd chunks march down (down = true): all chunks of a column
+// run in the same wave or two, and the z-halo planes two neighbouring chunks share
+// are then read by both at the same time (both at their start or both at their end),
+// from L2 once, instead of a whole chunk duration apart (128^3 F32 +1.2 %, E6 slab
+// +1.8 %).  The 3-D grid runs chunk after chunk in many waves: there a chunk that
+// starts where the previous wave's chunk ended finds its halo planes in L2, so every
+// chunk marches up (alternating there measured 1 % slower at 256^3).
 template <class CT>
-__device__ __forceinline__ void block_work(const StepArgs<CT> &a, int &bx, int &by, int &z0, int &zend) {
+__device__ __forceinline__ void block_work(const StepArgs<CT> &a, int &bx, int &by, int &z0, int &zend,
+                                           bool &down) {
   if (a.zbal_k > 0) {
     const int b = blockIdx.x, C = a.zbal_cols, K = a.zbal_k;
     int j, c;
@@ -254,17 +262,20 @@ __device__ __forceinline__ void block_work(const StepArgs<CT> &a, int &bx, int &
     zend = (int)((int64_t)(j + 1) * a.nz / kc);
     by = c / a.zbal_cols_x;
     bx = c - by * a.zbal_cols_x;
+    down = (j & 1) != 0;
   } else {
     bx = blockIdx.x;
     by = blockIdx.y;
     z0 = blockIdx.z * a.tile_z;
     zend = min(z0 + a.tile_z, a.nz);
+    down = false;
   }
 }
 
-// One block's work: the column (bx, by), planes z0 .. zend - 1, of the lattice described by a.
+// One block's work: the column (bx, by), planes z0 .. zend - 1, of the lattice described by a,
+// marched upward or (down) downward.
 template <int LAT, int STEN, class ST, class CT, int TY>
-__device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by, int z0, int zend,
+__device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by, int z0, int zend, bool down,
                                            unsigned char *smem_raw) {
   using L = Lattice<LAT>;
   using SN = Stencil<LAT, STEN>;
@@ -294,7 +305,9 @@ __device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by
 
   P2<CT> cur[Q], nxt[Q];
   int slot = 0;
-  for (int p = z0 - HZ; p <= zend - 1 + HZ; ++p) {
+  const int np = zend - z0 + 2 * HZ;  // planes z0 - HZ .. zend - 1 + HZ, in march order m
+  for (int m = 0; m < np; ++m) {
+    const int p = down ? zend - 1 + HZ - m : z0 - HZ + m;
     const int gz = ((p % nz) + nz) % nz;
     // ---- density / psi deviations of this plane: own site
     {
@@ -324,12 +337,12 @@ __device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by
     }
     __syncthreads();
 
-    // ---- collide plane c once planes c - HZ .. c + HZ are in the ring
-    const int c = p - HZ;
-    if (c >= z0) {
-      int sl[2 * HZ + 1];
+    // ---- collide plane c (march position m - HZ) once planes c - HZ .. c + HZ are in the ring
+    if (m >= 2 * HZ) {
+      const int c = down ? p + HZ : p - HZ;
+      int sl[2 * HZ + 1];  // ring slot of plane c - HZ + d, at march position m - 2 HZ + d (m - d down)
 #pragma unroll
-      for (int d = 0; d <= 2 * HZ; ++d) sl[d] = (slot - 2 * HZ + d + 2 * NPL) % NPL;  // plane c - HZ + d
+      for (int d = 0; d <= 2 * HZ; ++d) sl[d] = (down ? slot - d + NPL : slot - 2 * HZ + d + 2 * NPL) % NPL;
       const int gzc = ((c % nz) + nz) % nz;
       const int64_t site = (int64_t)gx + (int64_t)nx * (gy + (int64_t)ny * gzc);
       if (HZ == 1) {
@@ -351,8 +364,9 @@ template <int LAT, int STEN, class ST, class CT, int TY>
 __global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 16 / TY)) sc_step_kernel(const StepArgs<CT> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   int bx, by, z0, zend;
-  block_work(a, bx, by, z0, zend);
-  step_block<LAT, STEN, ST, CT, TY>(a, bx, by, z0, zend, smem_raw);
+  bool down;
+  block_work(a, bx, by, z0, zend, down);
+  step_block<LAT, STEN, ST, CT, TY>(a, bx, by, z0, zend, down, smem_raw);
 }
 
 // Batched form: one launch steps several lattices.  Block b works on item
@@ -373,7 +387,7 @@ __global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 16 / TY))
     a.ndst = const_cast<float2 *>(u);
   }
   const int z0 = it.w * a.tile_z;
-  step_block<LAT, STEN, ST, CT, TY>(a, it.y, it.z, z0, min(z0 + a.tile_z, a.nz), smem_raw);
+  step_block<LAT, STEN, ST, CT, TY>(a, it.y, it.z, z0, min(z0 + a.tile_z, a.nz), false, smem_raw);
 }
 
 }  // namespace scgb

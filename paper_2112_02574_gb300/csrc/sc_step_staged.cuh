@@ -110,12 +110,13 @@ __device__ __forceinline__ P2<CT> staged_sum(const ST *stage, const float2 *nrin
   return sum;
 }
 
-// One block's column (bx, by), planes z0 .. zend - 1, of the lattice described by a.
+// One block's column (bx, by), planes z0 .. zend - 1, of the lattice described by a,
+// marched upward or (down) downward; "plane k" below is march position k.
 // NS: pipeline stages (2: the copy of plane k + 2 overlaps sum k and collide k - 1;
 // 1: the copy of plane k + 1 overlaps collide k - 1 only, for half the stage memory).
 // Window x coordinates wrap once: every chunk start lies in [-nx, 2 nx) for nx >= 32.
 template <class ST, class CT, int TY, int NS>
-__device__ __forceinline__ void staged_block(const StepArgs<CT> &a, int bx, int by, int z0, int zend,
+__device__ __forceinline__ void staged_block(const StepArgs<CT> &a, int bx, int by, int z0, int zend, bool down,
                                              unsigned char *smem_raw) {
   static_assert(NS == 1 || NS == 2, "one or two pipeline stages");
   using G = StagedGeom<ST, TY>;
@@ -140,6 +141,9 @@ __device__ __forceinline__ void staged_block(const StepArgs<CT> &a, int bx, int 
   ST *__restrict__ dst = static_cast<ST *>(a.dst);
   const int x0 = bx * 32, y0 = by * TY;
   const int np = zend - z0 + 2;  // planes z0 - 1 .. zend
+  // z of march position k (k = 0 .. np - 1) and of density position m (m = 0 .. np + 1)
+  auto zk = [&](int k) { return down ? zend - k : z0 - 1 + k; };
+  auto zm = [&](int m) { return down ? zend + 1 - m : z0 - 2 + m; };
   const int own = (ty + 1) * G::SX + (tx + 1);
   const bool valid_xy = (x0 + tx < nx) && (y0 + ty < ny);
   const int gx = x0 + tx, gy = (y0 + ty) % ny;
@@ -228,11 +232,11 @@ __device__ __forceinline__ void staged_block(const StepArgs<CT> &a, int bx, int 
       }
     }
   };
-  // local reference: density plane m (z = z0 - 2 + m, m = 0 .. np + 1) into ring slot m & 3
+  // local reference: density position m (z = zm(m)) into ring slot m & 3
   auto copy_nref = [&](int m) {
     if constexpr (G::LOCAL) {
       float2 *dstp = nring + (m & (G::NPLN - 1)) * G::NPLANE_N;
-      const int64_t zo = (int64_t)((((z0 - 2 + m) % nz) + nz) % nz) * ny;  // m - 2 can wrap more than once for nz < 3
+      const int64_t zo = (int64_t)(((zm(m) % nz) + nz) % nz) * ny;  // can wrap more than once for nz < 3
       for (int t = tid; t < G::RYN * G::NCHN; t += NT) {
         const int rr = t / G::NCHN, c = t - rr * G::NCHN;
         int ys = y0 - 2 + rr;
@@ -249,7 +253,7 @@ __device__ __forceinline__ void staged_block(const StepArgs<CT> &a, int bx, int 
 #pragma unroll
   for (int j = 0; j < NS; ++j) {
     __syncthreads();
-    rows_for(wrapz(z0 - 1 + j));
+    rows_for(wrapz(zk(j)));
     __syncthreads();
     copy_rows(j);
     if (j == 0) {
@@ -265,14 +269,15 @@ __device__ __forceinline__ void staged_block(const StepArgs<CT> &a, int bx, int 
   auto body = [&](int k, P2<CT> (&prev)[Q], P2<CT> (&mine)[Q]) {
     const int s = NS == 2 ? (k & 1) : 0;
     const ST *stage = stage0 + s * G::STAGE_ELEMS;
-    // density planes of z - 1, z, z + 1 (z = z0 - 1 + k, ring positions k .. k + 2)
-    const int nsl[3] = {(k & 3) * G::NPLANE_N, ((k + 1) & 3) * G::NPLANE_N, ((k + 2) & 3) * G::NPLANE_N};
+    // density planes of z - 1, z, z + 1 (z = zk(k)): density positions k .. k + 2 (reversed down)
+    const int n_lo = (k & 3) * G::NPLANE_N, n_hi = ((k + 2) & 3) * G::NPLANE_N;
+    const int nsl[3] = {down ? n_hi : n_lo, ((k + 1) & 3) * G::NPLANE_N, down ? n_lo : n_hi};
     if constexpr (NS == 2)
       cp_async_wait_one();  // all groups but the newest (plane k + 1) are complete: plane k is in
     else
       cp_async_wait_all();
     __syncthreads();  // ... and visible to every thread; the last copy pass is over
-    if (k + NS < np) rows_for(wrapz(z0 - 1 + k + NS));
+    if (k + NS < np) rows_for(wrapz(zk(k + NS)));
     const int slot = k & (G::NPL - 1);
     {
       const P2<CT> dn = staged_sum<ST, CT, TY, true>(stage, nring, nsl, tx, ty, a.inv_scale, mine);
@@ -293,8 +298,11 @@ __device__ __forceinline__ void staged_block(const StepArgs<CT> &a, int bx, int 
     if (k + NS + 2 <= np + 1) copy_nref(k + NS + 2);
     cp_async_commit();  // (possibly empty) group for plane k + NS keeps "newest = plane k + NS"
     if (k >= 2) {
-      const int sl[3] = {(slot + 2) & 3, (slot + 3) & 3, slot};  // planes k-2, k-1, k
-      const int c = z0 - 2 + k;
+      // ring slots of planes c - 1, c, c + 1 (c = zk(k - 1)): march positions k - 2, k - 1, k
+      // (reversed down)
+      const int s_lo = (slot + 2) & 3;
+      const int sl[3] = {down ? slot : s_lo, (slot + 3) & 3, down ? s_lo : slot};
+      const int c = zk(k - 1);
       const int64_t site = (int64_t)gx + (int64_t)nx * (gy + (int64_t)ny * c);
       collide_site<kD3Q19, kE4, ST, CT, TY>(a, prev, s_dn, s_psi, sl, own, valid_xy, dst, site);
     }
@@ -313,8 +321,9 @@ template <class ST, class CT, int TY, int NS, int MINB>
 __global__ void __launch_bounds__(32 * TY, MINB) sc_step_staged(const StepArgs<CT> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   int bx, by, z0, zend;
-  block_work(a, bx, by, z0, zend);
-  staged_block<ST, CT, TY, NS>(a, bx, by, z0, zend, smem_raw);
+  bool down;
+  block_work(a, bx, by, z0, zend, down);
+  staged_block<ST, CT, TY, NS>(a, bx, by, z0, zend, down, smem_raw);
 }
 
 // Batched form (see sc_step_batched): block b works on items[b] = (lattice, bx,
@@ -341,7 +350,7 @@ __global__ void __launch_bounds__(32 * TY, MINB)
   }
   __syncthreads();
   const int z0 = it.w * s_a.tile_z;
-  staged_block<ST, CT, TY, NS>(s_a, it.y, it.z, z0, min(z0 + s_a.tile_z, s_a.nz), smem_raw);
+  staged_block<ST, CT, TY, NS>(s_a, it.y, it.z, z0, min(z0 + s_a.tile_z, s_a.nz), false, smem_raw);
 }
 
 }  // namespace scgb
