@@ -343,9 +343,12 @@ constexpr int kGenericTargetChunk = 16;
 // wave whenever the block count is not a multiple of the resident slots (staged, 128^3: 256
 // blocks of 32 planes for 304 slots; generic E6, 128^3: 320 blocks of 26 planes for 304).
 sc_status plan_z_split(sc_ctx *c) {
-  // staged 128^3 F32: 3 waves of 18-plane chunks beat 2 waves of 26 (+2 %); the generic
-  // kernel re-sums 2 HALO z-halo planes per chunk from L2 instead of a staged window
-  const int target_chunk = c->staged ? 18 : kGenericTargetChunk;
+  // Staged FP32, same box: 18 planes beat 12 and 36 at 128^3 (16.5 against 15.9 and 15.1 GLUPS)
+  // and tie with 36 at 160^3 and 192^3.  Staged 16-bit storage is issue-bound, so the two re-summed
+  // z-halo planes per chunk weigh more: 36 planes beat 18 by 2-3 % at 160^3 and 192^3 (equal at
+  // 128^3, one wave either way).  The generic kernel re-sums 2 HALO z-halo planes per chunk from
+  // L2 instead of a staged window.
+  const int target_chunk = !c->staged ? kGenericTargetChunk : (is_16bit(c->p.storage) ? 36 : 18);
   int dev = 0, sms = 0, occ = 0;
   const bool self_on = has_self(&c->p);
   const int lat = c->p.lattice == SC_D3Q19 ? kD3Q19 : kD2Q9, sten = c->p.stencil == SC_FORCE_E6 ? kE6 : kE4;
