@@ -231,10 +231,11 @@ def run_reference(args, rank, world):
     line = {"metric": METRIC, "value": value, "unit": "MLUPS", "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": dict(workload_config("f64"), time_steps_per_step=sample),
+            "data": "synthetic", "config": workload_config(args.storage),
             "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": oracle.threads(), "kind": "oracle",
-                             "sample": f"{sample} FP64 oracle time steps at 128^3 + radial profile + sigma[R] "
-                                       f"minimum per step"},
+                             "sample": f"each benchmark step a bounded sample of the workload: {sample} of its "
+                                       f"{INNER} time steps at 128^3 (FP64 oracle), then the radial profile "
+                                       f"and the sigma[R] minimum"},
             "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
