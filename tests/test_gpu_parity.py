@@ -248,6 +248,43 @@ def test_staged_thin_z_equals_generic(B, storage, nz):
     np.testing.assert_array_equal(outs[1], outs[0])
 
 
+@pytest.mark.parametrize("storage,u", [("F16", 2.0**-11), ("BF16", 2.0**-8)])
+@pytest.mark.parametrize("staged", [False, True])
+def test_sixteen_bit_storage_against_oracle(B, storage, u, staged):
+    """16-bit deviation storage against the FP64 oracle after k steps.  Each step
+    rounds every stored deviation from the site's rest equilibrium once, to
+    within u |g| (u the unit roundoff: 2^-11 FP16, 2^-8 BF16; FP16 carries a
+    power-of-two scale, so no value leaves the normal range), and the FP32
+    collision adds errors far below that.  Independent roundings of the 19
+    populations that feed each collision add like a random walk, so after k
+    steps the populations stay within 2 k u M of the oracle, M the largest
+    deviation |f_i - w_i n| of the oracle's state; the densities likewise.
+    The run prints the measured fraction of that bound."""
+    shape = (64, 12, 10)
+    k = 10
+    nA0, nB0 = S.droplet(shape[::-1], (32, 6, 5), 3.0, n_in=0.85, n_out=0.15, amplitude=1e-3)
+    kw = dict(tau=(1.0, 0.9), G=2.5, G_self=(-0.4, 0.0))
+    p = B.make_params(shape, psi_self=1, storage=getattr(B, f"SC_STORE_{storage}"), variant=2 if staged else 1, **kw)
+    sim = B.Simulation(p, nA0, nB0)
+    sim.step(k)
+    sim.sync()
+    assert sim.step_config["variant"] == (2 if staged else 1)
+    op = oracle.Params(shape=shape, lattice=1, psi_self=1, **kw)
+    f_orc = oracle.step(op, oracle.init(op, nA0, nB0), k)
+    _, w = oracle.velocity_set(1)
+    n_orc = f_orc.sum(axis=1)  # [2, N]
+    M = float(np.abs(f_orc - w[None, :, None] * n_orc[:, None, :]).max())
+    f_gpu = sim.populations().cpu().numpy()
+    err_f = float(np.abs(f_gpu - f_orc).max())
+    nA, nB, _ = sim.moments(with_u=False)
+    err_n = max(float(np.abs(nA.cpu().numpy() - n_orc[0]).max()), float(np.abs(nB.cpu().numpy() - n_orc[1]).max()))
+    bound = 2 * k * u * M
+    print(f"{storage} staged={staged}: max |df| = {err_f:.3e} ({err_f / bound:.3f} of 2 k u M), "
+          f"max |dn| = {err_n:.3e} ({err_n / bound:.3f}), M = {M:.3e}")
+    assert err_f <= bound
+    assert err_n <= bound
+
+
 def test_swap_symmetry_bitwise(B):
     """Section 2: G_AA = G_BB and tau_A = tau_B make A <-> B an exact symmetry."""
     shape = (40, 12, 9)
