@@ -28,8 +28,11 @@ namespace scgb {
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+// 16-byte copy global -> shared, cached in L2 only; the L2::256B prefetch-size hint lets an L2
+// miss fetch the whole aligned 256-byte block (a row window spans 288 B and more): same-box
+// +1.0 % at 256^3 and +0.4 % at 128^3 in FP32 against no hint, L2::128B unchanged.
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+  asm volatile("cp.async.cg.shared.global.L2::256B [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
