@@ -11,23 +11,37 @@ import torch
 
 from . import binding as B
 
-STAGED = [(2, 4, 16, 2, 2), (2, 4, 16, 2, 3), (2, 4, 16, 1, 2), (2, 4, 16, 1, 3), (2, 4, 32, 1, 3),
-          (2, 4, 8, 1, 3), (2, 8, 16, 2, 1), (2, 8, 16, 1, 2)]
-GENERIC = [(1, 4, 16, 0, 0), (1, 4, 32, 0, 0), (1, 8, 16, 0, 0), (1, 8, 32, 0, 0), (1, 2, 32, 0, 0)]
+# (variant, tile_y, tile_z, stages, blocks_per_sm); 0 = the library's choice.  The first
+# candidate is the library default, so the tuner never returns a slower configuration than it.
+DEFAULT = [(0, 0, 0, 0, 0)]
+STAGED = [(2, 4, 0, 1, 3), (2, 4, 0, 2, 2), (2, 4, 16, 1, 3), (2, 4, 32, 1, 3), (2, 4, 16, 2, 3),
+          (2, 8, 0, 1, 2), (2, 8, 0, 1, 1), (2, 8, 16, 2, 1), (2, 8, 32, 1, 2)]
+GENERIC = [(1, 8, 0, 0, 0), (1, 4, 0, 0, 0), (1, 8, 16, 0, 0), (1, 8, 32, 0, 0), (1, 4, 32, 0, 0)]
+CHUNK_SITES = {B.SC_STORE_F64: 1, B.SC_STORE_F32: 2, B.SC_STORE_F16: 4, B.SC_STORE_BF16: 4}
 
 
 def staged_eligible(params) -> bool:
-    return (params.lattice == B.SC_D3Q19 and params.stencil == B.SC_FORCE_E4 and params.nx % 32 == 0
-            and params.nx >= 64)
+    """The library's rule for the cp.async-staged kernel: D3Q19, E4, nx >= 32 and a multiple of the
+    sites in one 16-byte copy chunk of the storage."""
+    return (params.lattice == B.SC_D3Q19 and params.stencil == B.SC_FORCE_E4 and params.nx >= 32
+            and params.nx % CHUNK_SITES[params.storage] == 0)
+
+
+def candidates_for(params):
+    """The candidate list tune_step uses by default for these parameters."""
+    cands = DEFAULT + (STAGED if staged_eligible(params) else []) + GENERIC
+    if params.storage == B.SC_STORE_F64:  # staged F64: tile_y 4 only
+        cands = [c for c in cands if not (c[0] == 2 and c[1] != 4)]
+    if params.lattice == B.SC_D2Q9:  # one plane: tile_z is irrelevant
+        cands = [c for c in cands if c[0] != 2 and c[2] in (0, 16)]
+    return cands
 
 
 def tune_step(params, nA0, nB0, candidates=None, steps: int = 64, warmup: int = 8, device="cuda"):
     """Returns ((variant, tile_y, tile_z, stages, blocks_per_sm), ms_per_step, table) for the
     fastest candidate."""
     if candidates is None:
-        candidates = (STAGED if staged_eligible(params) else []) + GENERIC
-    if params.storage == B.SC_STORE_F64:
-        candidates = [c for c in candidates if not (c[0] == 2 and c[1] != 4)]
+        candidates = candidates_for(params)
     table = []
     for variant, ty, tz, ns, mb in candidates:
         p = B.make_params((params.nx, params.ny, params.nz), lattice=params.lattice, stencil=params.stencil,

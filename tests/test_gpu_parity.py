@@ -285,6 +285,31 @@ def test_sixteen_bit_storage_against_oracle(B, storage, u, staged):
     assert err_n <= bound
 
 
+@pytest.mark.parametrize("storage", ["F32", "F16"])
+def test_tuner_choice_changes_speed_only(B, storage):
+    """The single-lattice autotuner times every candidate it lists (the library
+    default first) and returns the fastest; that configuration computes the
+    default's state bit for bit."""
+    from paper_2112_02574_gb300 import tune
+
+    st = getattr(B, f"SC_STORE_{storage}")
+    shape = (64, 24, 40)
+    f = S.droplet(shape[::-1], (32, 12, 20), 6.0, n_in=0.85, n_out=0.15, amplitude=1e-3)
+    kw = dict(psi_self=1, storage=st, tau=(1.0, 0.9), G=2.5, G_self=(-0.4, 0.0))
+    p = B.make_params(shape, **kw)
+    best, ms, table = tune.tune_step(p, *f, steps=8, warmup=2)
+    assert [c for c, _ in table] == tune.candidates_for(p)
+    assert all(t > 0 for _, t in table) and ms == min(t for _, t in table)
+    outs = []
+    for variant, ty, tz, ns, mb in ((0, 0, 0, 0, 0), best):
+        sim = B.Simulation(B.make_params(shape, tile_y=ty, tile_z=tz, variant=variant, stages=ns, blocks_per_sm=mb,
+                                         **kw), *f)
+        sim.step(7)
+        sim.sync()
+        outs.append(sim.state().cpu().numpy())
+    np.testing.assert_array_equal(outs[1], outs[0])
+
+
 def test_swap_symmetry_bitwise(B):
     """Section 2: G_AA = G_BB and tau_A = tau_B make A <-> B an exact symmetry."""
     shape = (40, 12, 9)
