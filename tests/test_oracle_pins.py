@@ -107,29 +107,39 @@ def test_force_on_sine_wave_closed_form(orc, stencil):
     assert np.abs(FB).max() < 1e-15  # n_A uniform: no force on B
 
 
-def test_self_force_and_pressure_tensor_closed_form(orc):
-    """Eq. sm:pt on n_A = a + b sin(kx), n_B = 0, psi = n, G_AA only:
-    P^xx = c_s^2 n + G_AA c_s^2/2 n (a + b sin(kx) cos k),
-    P^yy = P^zz = c_s^2 n + G_AA c_s^2/2 n (a + b sin(kx)(2 + cos k)/3), off-diagonals 0;
-    and Eq. sc_force gives F^x = -G_AA c_s^2 n b cos(kx) sin k."""
+@pytest.mark.parametrize("stencil", [0, 1])
+def test_self_force_and_pressure_tensor_closed_form(orc, stencil):
+    """Eq. sm:pt on n_A = a + b sin(kx), n_B = 0, psi = n, G_AA only: with
+    X(k) = sum_a W xi_x^2 cos(k xi_x) and Y(k) = sum_a W xi_y^2 cos(k xi_x),
+    P^xx = c_s^2 n + G_AA c_s^2/2 n (a + b sin(kx) X(k)),
+    P^yy = P^zz = c_s^2 n + G_AA c_s^2/2 n (a + b sin(kx) Y(k)), off-diagonals 0;
+    and Eq. sc_force gives F^x = -G_AA c_s^2 n b cos(kx) S(k).  Counting the
+    stencil's vectors by their x component: E4 X = cos k, Y = (2 + cos k)/3,
+    S = sin k; E6 (shells 1-4, W = 2/15, 1/15, 1/60, 1/120) X = 14/15 cos k +
+    1/15 cos 2k, Y = 3/5 + 2/5 cos k, S = 14/15 sin k + 1/30 sin 2k."""
     L = 12
-    p = params(orc, (L, 3, 3), lattice=1, psi_self=0, G=0.0, G_self=(-1.3, 0.0))
+    p = params(orc, (L, 5, 5), lattice=1, stencil=stencil, psi_self=0, G=0.0, G_self=(-1.3, 0.0))
     k = 2 * math.pi / L
     x = np.arange(L)
     a, b = 0.7, 0.2
     n = a + b * np.sin(k * x)
-    nA = np.broadcast_to(n, (3, 3, L)).reshape(-1)
+    nA = np.broadcast_to(n, (5, 5, L)).reshape(-1)
     nB = np.zeros(p.n_sites)
-    P = orc.pressure_tensor(p, nA, nB).reshape(6, 3, 3, L)[:, 0, 0]
+    if stencil == 0:
+        X, Y, Sk = math.cos(k), (2 + math.cos(k)) / 3, math.sin(k)
+    else:
+        X = 14 / 15 * math.cos(k) + 1 / 15 * math.cos(2 * k)
+        Y = 3 / 5 + 2 / 5 * math.cos(k)
+        Sk = 14 / 15 * math.sin(k) + 1 / 30 * math.sin(2 * k)
+    P = orc.pressure_tensor(p, nA, nB).reshape(6, 5, 5, L)[:, 0, 0]
     cs2, G = GOLD["cs2"]["value"], -1.3
-    np.testing.assert_allclose(P[0], cs2 * n + 0.5 * G * cs2 * n * (a + b * np.sin(k * x) * math.cos(k)), atol=1e-15)
-    pyy = cs2 * n + 0.5 * G * cs2 * n * (a + b * np.sin(k * x) * (2 + math.cos(k)) / 3)
+    np.testing.assert_allclose(P[0], cs2 * n + 0.5 * G * cs2 * n * (a + b * np.sin(k * x) * X), atol=1e-15)
+    pyy = cs2 * n + 0.5 * G * cs2 * n * (a + b * np.sin(k * x) * Y)
     np.testing.assert_allclose(P[1], pyy, atol=1e-15)
     np.testing.assert_allclose(P[2], pyy, atol=1e-15)
     assert np.abs(P[3:]).max() < 1e-15
     FA, _ = orc.force(p, nA, nB)
-    np.testing.assert_allclose(FA[0].reshape(3, 3, L)[0, 0], -G * cs2 * n * b * np.cos(k * x) * math.sin(k),
-                               atol=1e-15)
+    np.testing.assert_allclose(FA[0].reshape(5, 5, L)[0, 0], -G * cs2 * n * b * np.cos(k * x) * Sk, atol=1e-15)
 
 
 @pytest.mark.parametrize("psi_self,stencil", [(0, 0), (1, 0), (1, 1)])
