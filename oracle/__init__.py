@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY.  This package is the slow reference the CUDA library
 is checked against; only the test suite, the smoke check and the benchmark's
-CPU-baseline leg may import it.  It shares no code with the CUDA library and
+CPU-baseline leg and reference arm may import it.  It shares no code with the CUDA library and
 never imports it.
 
 * ``sc_oracle.c`` -- the lattice Boltzmann step (section 2: Eqs. lbm, omega_i,

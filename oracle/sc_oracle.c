@@ -5,7 +5,8 @@
  *
  * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct
  * reference that the CUDA library is checked against.  Only the test suite,
- * the smoke check and the benchmark's CPU-baseline leg may load it.  It shares
+ * the smoke check and the benchmark's CPU-baseline leg and reference arm may
+ * load it.  It shares
  * no code, header or table with the CUDA library: every table below is written
  * out here by hand from the paper.
  *
