@@ -351,3 +351,196 @@ def test_profile_radial_bins_brute_force(orc):
             assert rows[b, 2] == pytest.approx(orc.bulk_pressure(p, 0.6, 0.3), rel=1e-14)
         else:
             assert not rows[b].any()
+
+
+# ------------------------------------- off-diagonal pressure tensor and the profile projections
+def _diagonal_wave(L, k, a, b, axes):
+    """psi = n_A = a + b sin(theta), theta = k * (sum of the listed coordinates), on an L^3 box
+    (site order x fastest); returns (n_A as [L, L, L] indexed [z, y, x], theta)."""
+    z, y, x = np.meshgrid(np.arange(L), np.arange(L), np.arange(L), indexing="ij")
+    coord = {"x": x, "y": y, "z": z}
+    theta = k * sum(coord[c] for c in axes)
+    return a + b * np.sin(theta), theta
+
+
+def test_pressure_tensor_off_diagonal_closed_form(orc):
+    """Eq. sm:pt with psi = n, G_AA only, nearest-neighbour stencil (W = 1/6, 1/12), on a wave
+    along the body diagonal, n = a + b sin(theta), theta = k (x + y + z).  Counting the 18
+    vectors: only the four xi = (+-1, +-1, 0) weigh xi_x xi_y; (1, 1, 0) and (-1, -1, 0) see
+    theta +- 2k, (1, -1, 0) and (-1, 1, 0) see theta, so sum_a W xi_x xi_y n(x + xi_a) =
+    (b / 6) sin(theta) (cos 2k - 1), and by symmetry the same for xz and yz.  Each diagonal
+    collects 2 vectors at theta +- k (W = 1/6) and 8 at theta +- 2k, theta (W = 1/12):
+    sum_a W xi_x^2 n(x + xi_a) = a + b sin(theta) (1 + cos k + cos 2k) / 3.  So
+    P^mumu = c_s^2 n + G c_s^2/2 n (a + b sin(theta) (1 + cos k + cos 2k)/3) and
+    P^munu = G c_s^2/2 n (b / 6) sin(theta) (cos 2k - 1) for mu != nu."""
+    L = 12
+    k = 2 * math.pi / L
+    a, b, G = 0.7, 0.2, -1.3
+    n, th = _diagonal_wave(L, k, a, b, "xyz")
+    p = params(orc, (L, L, L), lattice=1, stencil=0, psi_self=0, G=0.0, G_self=(G, 0.0))
+    P = orc.pressure_tensor(p, n.ravel(), np.zeros(L**3)).reshape(6, L, L, L)
+    cs2 = GOLD["cs2"]["value"]
+    diag = cs2 * n + 0.5 * G * cs2 * n * (a + b * np.sin(th) * (1 + math.cos(k) + math.cos(2 * k)) / 3)
+    off = 0.5 * G * cs2 * n * (b / 6) * np.sin(th) * (math.cos(2 * k) - 1)
+    assert np.abs(off).max() > 1e-3  # the off-diagonals are far from zero here
+    for c in range(3):
+        np.testing.assert_allclose(P[c], diag, atol=1e-15)
+    for c in range(3, 6):
+        np.testing.assert_allclose(P[c], off, atol=1e-15)
+
+
+def test_pressure_tensor_planar_diagonal_wave_closed_form(orc):
+    """As above with theta = k (x + y): P^xy = G c_s^2/2 n (b/6) sin(theta)(cos 2k - 1),
+    P^xz = P^yz = 0 (the (+-1, 0, +-1) vectors cancel in pairs), P^xx = P^yy with
+    sum_a W xi_x^2 n(x + xi_a) = a + b sin(theta) ((2/3) cos k + (1/6) cos 2k + 1/6) and
+    P^zz with sum_a W xi_z^2 n(x + xi_a) = a + b sin(theta) (1/3 + (2/3) cos k)."""
+    L = 12
+    k = 2 * math.pi / L
+    a, b, G = 0.6, 0.25, 0.9
+    n, th = _diagonal_wave(L, k, a, b, "xy")
+    p = params(orc, (L, L, L), lattice=1, stencil=0, psi_self=0, G=0.0, G_self=(G, 0.0))
+    P = orc.pressure_tensor(p, n.ravel(), np.zeros(L**3)).reshape(6, L, L, L)
+    cs2 = GOLD["cs2"]["value"]
+    s = np.sin(th)
+    pxx = cs2 * n + 0.5 * G * cs2 * n * (a + b * s * (2 / 3 * math.cos(k) + math.cos(2 * k) / 6 + 1 / 6))
+    pzz = cs2 * n + 0.5 * G * cs2 * n * (a + b * s * (1 / 3 + 2 / 3 * math.cos(k)))
+    pxy = 0.5 * G * cs2 * n * (b / 6) * s * (math.cos(2 * k) - 1)
+    np.testing.assert_allclose(P[0], pxx, atol=1e-15)
+    np.testing.assert_allclose(P[1], pxx, atol=1e-15)
+    np.testing.assert_allclose(P[2], pzz, atol=1e-15)
+    np.testing.assert_allclose(P[3], pxy, atol=1e-15)
+    assert np.abs(P[4:]).max() < 1e-15
+
+
+def _min_image_displacement(shape_zyx, centre):
+    """(dx, dy, dz) [3, N] from centre (x, y, z) to every site, each in [-L/2, L/2) by
+    brute force over the periodic images -L, 0, +L."""
+    nz, ny, nx = shape_zyx
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    out = []
+    for c, L, ce in ((x, nx, centre[0]), (y, ny, centre[1]), (z, nz, centre[2])):
+        cand = np.stack([c - ce - L, c - ce, c - ce + L]).astype(float)
+        ok = (cand >= -L / 2) & (cand < L / 2)
+        out.append((cand * ok).sum(0).ravel())
+    return np.array(out)
+
+
+def _radial_brute_force(shape_zyx, centre, bin_width, nbins, Pfull, nA, nB):
+    """Section 3's decomposition done site by site: r from the minimum image, the unit vector
+    rhat, P_N = rhat . P . rhat with the full symmetric 3 x 3 matrix, P_T = (tr P - P_N) / 2
+    (tr P / 3 for both at r = 0), then per-bin means of (r, P_N, P_T, n_A, n_B) and counts.
+    Pfull: [3, 3, N]."""
+    d = _min_image_displacement(shape_zyx, centre)  # [3, N] as (dx, dy, dz)
+    r = np.sqrt((d**2).sum(0))
+    with np.errstate(invalid="ignore", divide="ignore"):
+        e = np.where(r > 0, d / r, 0.0)
+    tr = Pfull[0, 0] + Pfull[1, 1] + Pfull[2, 2]
+    PN = np.einsum("ms,mns,ns->s", e, Pfull, e)
+    PN = np.where(r > 0, PN, tr / 3)
+    PT = np.where(r > 0, (tr - PN) / 2, tr / 3)
+    kbin = np.floor(r / bin_width).astype(int)
+    keep = kbin < nbins
+    out = np.zeros((nbins, 6))
+    cnt = np.bincount(kbin[keep], minlength=nbins)[:nbins]
+    for c, v in enumerate((r, PN, PT, nA, nB)):
+        s = np.bincount(kbin[keep], weights=v[keep], minlength=nbins)[:nbins]
+        out[:, c] = np.where(cnt > 0, s / np.maximum(cnt, 1), 0.0)
+    out[:, 5] = cnt
+    return out
+
+
+def _full_matrix(P6):
+    """[6, N] (xx, yy, zz, xy, xz, yz) -> [3, 3, N]."""
+    xx, yy, zz, xy, xz, yz = P6
+    return np.array([[xx, xy, xz], [xy, yy, yz], [xz, yz, zz]])
+
+
+def test_radial_profile_projection_on_closed_form_tensor(orc):
+    """Eq. pt_projection on the body-diagonal wave, where the off-diagonal components are of
+    the same order as the anisotropic part of the diagonal: the oracle's radial rows equal the
+    brute-force projection rhat . P . rhat of the closed-form tensor (no oracle tensor used),
+    binned by hand.  A dropped factor 2 on the off-diagonal terms moves P_N by
+    sum_{mu != nu} rhat_mu rhat_nu P^munu / 2, several times the tolerance."""
+    L = 12
+    k = 2 * math.pi / L
+    a, b, G = 0.7, 0.2, -1.3
+    n, th = _diagonal_wave(L, k, a, b, "xyz")
+    cs2 = GOLD["cs2"]["value"]
+    diag = (cs2 * n + 0.5 * G * cs2 * n * (a + b * np.sin(th) * (1 + math.cos(k) + math.cos(2 * k)) / 3)).ravel()
+    off = (0.5 * G * cs2 * n * (b / 6) * np.sin(th) * (math.cos(2 * k) - 1)).ravel()
+    P6 = np.array([diag, diag, diag, off, off, off])
+    centre = (5.0, 4.0, 7.0)
+    p = params(orc, (L, L, L), lattice=1, stencil=0, psi_self=0, G=0.0, G_self=(G, 0.0))
+    rows = orc.profile(p, n.ravel(), np.zeros(L**3), orc.RADIAL, centre=centre, bin_width=0.5, nbins=24)
+    want = _radial_brute_force((L, L, L), centre, 0.5, 24, _full_matrix(P6), n.ravel(), np.zeros(L**3))
+    np.testing.assert_array_equal(rows[:, 5], want[:, 5])
+    np.testing.assert_allclose(rows[:, :5], want[:, :5], rtol=0, atol=1e-14)
+    # the off-diagonal share of P_N is resolved: halving it would move some bin by far more than 1e-14
+    half = _radial_brute_force((L, L, L), centre, 0.5, 24, _full_matrix(P6 * np.array([1, 1, 1, .5, .5, .5])[:, None]),
+                               n.ravel(), np.zeros(L**3))
+    assert np.abs(half[:, 1] - want[:, 1]).max() > 1e-4
+
+
+def test_radial_profile_projection_on_droplet(orc):
+    """Eq. pt_projection on a non-uniform, off-centre, noisy two-component droplet with both
+    couplings and psi = exp(-1/n): every radial row (count, mean r, P_N, P_T, n_A, n_B) equals
+    the brute-force projection of the pinned Eq. sm:pt tensor with the full 3 x 3 matrix, and
+    P_T is (tr P - P_N) / 2 bin by bin (the trace binned on its own)."""
+    shape = (14, 13, 12)  # (nz, ny, nx)
+    nA, nB = S.droplet(shape, (5, 7, 6), 3.5, n_in=0.85, n_out=0.15, amplitude=2e-2)
+    p = params(orc, shape[::-1], lattice=1, stencil=0, psi_self=1, G=2.5, G_self=(-0.6, 0.3))
+    f = orc.step(p, orc.init(p, nA, nB), 20)
+    a, bB, _ = orc.moments(p, f, with_u=False)
+    P6 = orc.pressure_tensor(p, a, bB)
+    assert np.abs(P6[3:]).max() > 1e-3
+    centre = (6.0, 7.0, 5.0)
+    rows = orc.profile(p, a, bB, orc.RADIAL, centre=centre, bin_width=0.5, nbins=20)
+    want = _radial_brute_force(shape, centre, 0.5, 20, _full_matrix(P6), a, bB)
+    np.testing.assert_array_equal(rows[:, 5], want[:, 5])
+    np.testing.assert_allclose(rows[:, :5], want[:, :5], rtol=0, atol=1e-14)
+    tr = P6[0] + P6[1] + P6[2]
+    d = _min_image_displacement(shape, centre)
+    r = np.sqrt((d**2).sum(0))
+    kb = np.floor(r / 0.5).astype(int)
+    m = kb < 20
+    trbin = np.bincount(kb[m], weights=tr[m], minlength=20)[:20] / np.maximum(rows[:, 5], 1)
+    nz = rows[:, 5] > 0
+    np.testing.assert_allclose(rows[nz, 2], (trbin[nz] - rows[nz, 1]) / 2, rtol=0, atol=1e-14)
+
+
+def test_axis_profile_is_section3_line(orc):
+    """Section 3's estimator along the x axis through the centre node: row k is the site
+    (c_x + k, c_y, c_z) with coordinate k, P_N = P^xx, P_T = P^yy, its densities and count 1.
+    On the x wave of the closed-form test (P^xx and P^yy differ there) the rows equal the closed
+    forms; on a noisy off-centre droplet they equal the pinned tensor at those sites."""
+    L = 12
+    k = 2 * math.pi / L
+    a, b, G = 0.7, 0.2, -1.3
+    p = params(orc, (L, 5, 5), lattice=1, stencil=0, psi_self=0, G=0.0, G_self=(G, 0.0))
+    x = np.arange(L)
+    n = a + b * np.sin(k * x)
+    nA = np.broadcast_to(n, (5, 5, L)).reshape(-1)
+    cs2 = GOLD["cs2"]["value"]
+    pxx = cs2 * n + 0.5 * G * cs2 * n * (a + b * np.sin(k * x) * math.cos(k))
+    pyy = cs2 * n + 0.5 * G * cs2 * n * (a + b * np.sin(k * x) * (2 + math.cos(k)) / 3)
+    cx = 3
+    rows = orc.profile(p, nA, np.zeros(p.n_sites), orc.AXIS_X, centre=(cx, 2, 1), nbins=L - cx)
+    xs = cx + np.arange(L - cx)
+    np.testing.assert_array_equal(rows[:, 0], np.arange(L - cx))
+    np.testing.assert_allclose(rows[:, 1], pxx[xs], atol=1e-15)
+    np.testing.assert_allclose(rows[:, 2], pyy[xs], atol=1e-15)
+    np.testing.assert_allclose(rows[:, 3], n[xs], atol=1e-15)
+    assert not rows[:, 4].any() and (rows[:, 5] == 1).all()
+
+    shape = (9, 10, 16)  # (nz, ny, nx)
+    nA, nB = S.droplet(shape, (4, 5, 8), 3.0, n_in=0.85, n_out=0.15, amplitude=2e-2)
+    p = params(orc, shape[::-1], lattice=1, stencil=0, psi_self=1, G=2.5, G_self=(-0.6, 0.3))
+    P6 = orc.pressure_tensor(p, nA, nB).reshape(6, *shape)
+    c = (7, 4, 3)  # (x, y, z), not the droplet's centre
+    rows = orc.profile(p, nA, nB, orc.AXIS_X, centre=c, nbins=16 - c[0])
+    xs = c[0] + np.arange(16 - c[0])
+    np.testing.assert_array_equal(rows[:, 1], P6[0, c[2], c[1], xs])
+    np.testing.assert_array_equal(rows[:, 2], P6[1, c[2], c[1], xs])
+    np.testing.assert_array_equal(rows[:, 3], nA.reshape(shape)[c[2], c[1], xs])
+    np.testing.assert_array_equal(rows[:, 4], nB.reshape(shape)[c[2], c[1], xs])
+    assert np.abs(P6[0, c[2], c[1], xs] - P6[1, c[2], c[1], xs]).max() > 1e-3
