@@ -31,12 +31,12 @@ SHAPE = (128, 128, 128)
 RADIUS = 24.0
 G_CROSS = 3.6  # G c_s^2 = 1.2: the largest tested coupling that is stable in three dimensions at tau = 1
 INNER = 2048  # time steps per benchmark step (section 4: delta t = 2^11); --inner overrides for profiling
-# 2 comps x 19 pops x (read + write) x bytes, plus for 16-bit storage the FP32 reference-density pair of
-# each site (read + write, 16 B)
-BYTES_PER_SITE = {"f32": 304, "f16": 168, "bf16": 168, "f64": 608}
-# DRAM bytes (read + write) of one step launch on this workload, from an ncu capture
-# (profiles/sc_step_staged_d3q19_128cube.md); reported only while the kernel sources
-# still hash to the captured version.
+# algorithmic bytes per site update: 2 comps x 19 pops x (read + write) x storage bytes
+BYTES_PER_SITE = {"f32": 304, "f16": 152, "bf16": 152, "f64": 608}
+# bytes the 16-bit forms move in addition: the FP32 reference-density pair of each site (read + write)
+LOCAL_REF_BYTES = {"f16": 16, "bf16": 16}
+# DRAM bytes (read + write) of one step launch on this workload, from an ncu capture of the
+# launch; reported only while the kernel sources still hash to the captured version.
 KERNEL_SOURCES = ["paper_2112_02574_gb300/csrc/sc_common.cuh", "paper_2112_02574_gb300/csrc/sc_step_kernel.cuh",
                   "paper_2112_02574_gb300/csrc/sc_step_staged.cuh"]
 # DRAM bytes per step launch (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture), keyed by the
@@ -332,25 +332,31 @@ def run_gpu(args, rank, world, local_rank):
 
     value = whole_job_mlups(sites, INNER * args.steps, world, ms)
 
-    # end to end through the host-buffer entry point: H2D of the initial fields, INNER steps, D2H of the densities
+    # end to end through the host-buffer entry point, the same work as one benchmark step plus the copies:
+    # H2D of the initial fields, create, INNER steps, the radial profile, P_in / P_out and the sigma[R]
+    # minimum, D2H of the densities and the 8 results
     e2e = None
     if not args.no_e2e:
         ws = sim.workspace  # reuse the device workspace (the simulation above is finished)
         hA = torch.from_numpy(nA0.reshape(-1)).pin_memory()
         hB = torch.from_numpy(nB0.reshape(-1)).pin_memory()
         oA, oB = torch.empty_like(hA).pin_memory(), torch.empty_like(hB).pin_memory()
+        res = torch.empty(8, dtype=torch.float64).pin_memory()
+        run = lambda: B.sc_run_host_sigma(params, hA, hB, INNER, centre, 0.5, 128, oA, oB, res, ws, stream)
         with torch.cuda.stream(stream):
-            B.sc_run_host(params, hA, hB, INNER, oA, oB, ws, stream)  # warm
+            run()  # warm
             t0 = time.perf_counter()
             reps = max(1, args.steps // 2)
             for _ in range(reps):
-                B.sc_run_host(params, hA, hB, INNER, oA, oB, ws, stream)
+                run()
             e2e_s = (time.perf_counter() - t0) / reps
         if world > 1:
             e2e_s = max_over_ranks(e2e_s * 1e3, dev) * 1e-3
         e2e = {"value": whole_job_mlups(sites, INNER, world, e2e_s * 1e3), "unit": "MLUPS",
-               "h2d_bytes_per_step": 2 * sites * 8, "d2h_bytes_per_step": 2 * sites * 8,
-               "note": f"sc_run_host per step: H2D of n_A0, n_B0 (FP64), create, {INNER} steps, D2H of n_A, n_B"}
+               "h2d_bytes_per_step": 2 * sites * 8, "d2h_bytes_per_step": 2 * sites * 8 + 8 * 8,
+               "result": {"dP": float(res[0]), "R_s": float(res[2]), "sigma_s": float(res[3])},
+               "note": f"sc_run_host_sigma per step: H2D of n_A0, n_B0 (FP64), create, {INNER} steps, radial "
+                       f"profile + P_in, P_out + sigma[R] minimum, D2H of n_A, n_B and the 8 results"}
 
     precision = None
     if not args.no_precision and rank == 0:
@@ -376,7 +382,9 @@ def run_gpu(args, rank, world, local_rank):
                      "kernel": "sc_step_staged" if step_cfg["variant"] == 2 else "sc_step_kernel",
                      "launch": step_cfg,
                      "bytes_per_site": BYTES_PER_SITE[storage], "algorithmic_bytes_per_launch": alg_bytes,
-                     "kernel_ms": kern_ms, "peak_source": peak_kind},
+                     "kernel_ms": kern_ms, "peak_source": peak_kind,
+                     **({"frac_with_local_reference": (alg_bytes + LOCAL_REF_BYTES[storage] * sites)
+                         / (kern_ms * 1e-3) / 1e9 / peak} if storage in LOCAL_REF_BYTES else {})},
         "hbm_roofline_mlups_frac": value / world * 1e6 * BYTES_PER_SITE[storage] / (peak * 1e9),
         "gpu_launches": launches, "clocks": clk.summary(), "e2e": e2e, "precision": precision,
         "batch_sweep": batch,
@@ -744,6 +752,14 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # no launcher: start one rank per GPU on this node and pass the arguments through
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+               "--master-addr", "127.0.0.1", "--master-port", os.environ.get("MASTER_PORT", "29511"),
+               os.path.abspath(__file__), *sys.argv[1:]]
+        sys.exit(subprocess.call(cmd))
+    if args.gpus != world:
+        sys.exit(f"bench.py: --gpus {args.gpus} but the launcher started {world} rank(s)")
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

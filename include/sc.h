@@ -147,7 +147,8 @@ sc_status sc_set_state(sc_ctx *ctx, const void *src, size_t bytes);
  *             (decomposition of Eq. pt_projection, section 3);
  *   PLANAR_Z: one bin per plane z < nbins, P_N = <P^zz>, P_T = <(P^xx+P^yy)/2>
  *             (flat interface, section 4);
- *   AXIS_X:   sites (cx + k, cy, cz), k < nbins, P_N = P^xx, P_T = P^yy
+ *   AXIS_X:   sites (cx + k, cy, cz), k < nbins <= nx (larger nbins is
+ *             SC_EINVAL: each row holds exactly one site), P_N = P^xx, P_T = P^yy
  *             (section 3, the paper's own estimator).
  * Deterministic: per-block partial sums in a fixed order.  Asynchronous. */
 sc_status sc_pressure_profile(sc_ctx *ctx, int32_t kind, const double centre[3], double bin_width, int32_t nbins,
@@ -170,6 +171,38 @@ sc_status sc_bulk_pressure_at(sc_ctx *ctx, const int32_t node[3], double *out);
  * stream: cudaStream_t as void*.  Asynchronous. */
 sc_status sc_sigma_minimum(const double *rows, int32_t nbins, const double *P_in_out, int32_t dim, double R_lo,
                            double R_hi, double R_step, double *out, void *stream);
+
+/* The surface of tension of a droplet in one call: the pressure-tensor profile
+ * (as sc_pressure_profile), the bulk pressures of Eq. bulkp at the centre node
+ * (P_in) and at the far corner (nx-1, ny-1, nz-1) (P_out, section 4), and the
+ * minimum of the generalized surface tension sigma[R] (section 3, Eqs.
+ * gen_sigma and gen_d_sigma), all on the device.
+ *   kind:      SC_PROFILE_RADIAL (shells of bin_width around centre) or
+ *              SC_PROFILE_AXIS_X (the paper's line through the centre node,
+ *              unit spacing; bin_width is ignored); anything else is SC_EINVAL.
+ *   centre:    host [3] (x, y, z), or NULL for the centre node (nx/2, ny/2, nz/2);
+ *              the node nearest to it (periodic) gives P_in.
+ *   nbins:     rows of the profile (<= 4096; <= nx for the axis), or 0 for the
+ *              largest sphere inside the box (min(nx, ny, nz) / 2 / bin_width; the
+ *              axis: nx / 2 rows).
+ *   R_lo, R_hi, R_step: grid of the paper's interpolated minimum; 0 picks the
+ *              default for each (R_step 0.01, R_lo = R_step, R_hi = nbins x spacing).
+ *   out:       device FP64 [8] = (dP, C, R_s, sigma_s, R_grid, sigma_grid, P_in,
+ *              P_out), as sc_sigma_minimum.
+ *   rows:      device FP64 [nbins][6] that receives the profile, or NULL to keep
+ *              it in the context's workspace.
+ * Deterministic; asynchronous on the context's stream. */
+sc_status sc_surface_of_tension(sc_ctx *ctx, int32_t kind, const double centre[3], double bin_width, int32_t nbins,
+                                double R_lo, double R_hi, double R_step, double *out, double *rows);
+
+/* Run diagnostics of sections 2 and 4 in one call, deterministic FP64:
+ * out: device FP64 [10] = (mass_A, mass_B, momentum x, y, z (as sc_totals),
+ * dU (as sc_velocity_change: u_prev is read and then overwritten with u; NaN
+ * when u_prev is NULL), X, Y, Z, W (centre of mass of component `component`
+ * over `background`, as sc_centre_of_mass; all NaN when component is -1)).
+ * u_prev: device FP64 [3][N] or NULL; component: -1, 0 (A) or 1 (B).
+ * Asynchronous on the context's stream. */
+sc_status sc_diagnostics(sc_ctx *ctx, double *u_prev, int32_t component, double background, double *out);
 
 /* Convergence measure of section 4 on the velocity field: dU = (1 / N) sum over
  * the sites x of sum_alpha |u_alpha(x) - u_prev_alpha(x)|, with u the common
@@ -217,10 +250,15 @@ sc_status sc_curvature_fit(const double *Rs, const double *sigma_s, int32_t n, i
  * pseudopotential evaluated on the fly, and without a context or workspace.
  * Its only scratch is a fixed 4 MiB __device__ array inside this library, which
  * every GPU that loads the library holds until the process exits; nbins may be
- * at most 4096 (larger requests return SC_EINVAL).  It calls no cudaMalloc,
- * cudaFree or other allocating routine.  The first call on a device looks up
- * the array's device address (once per device, with that device current); make
- * that first call before any stream capture.  All calls share the array and
+ * at most 4096 (larger requests return SC_EINVAL), and at most nx for the x
+ * axis.  params must pass the model checks of sc_create (size, lattice,
+ * stencil, psi_self, finite couplings).  It calls no cudaMalloc, cudaFree or
+ * other allocating routine.  Every call made while its stream is not capturing
+ * looks up the array's device address on the current device (a device reset
+ * reloads the library's module and may move the array); a call made while the
+ * stream captures a CUDA graph reuses the address the last such lookup on that
+ * device found, so make the first call on a device, and the first after a
+ * device reset, before any stream capture.  All calls share the array and
  * each call overwrites every entry it later reads, so nothing needs clearing;
  * calls that overlap on the GPU (other streams, other host threads) race on
  * it.  out: device FP64 [nbins][6].  stream: cudaStream_t as void*.
@@ -242,6 +280,17 @@ sc_status sc_sync(sc_ctx *ctx);
  * The workspace is device memory as for sc_create.  Synchronous. */
 sc_status sc_run_host(const sc_params *params, const double *nA0, const double *nB0, int64_t nsteps, double *nA,
                       double *nB, void *workspace, size_t ws_bytes, void *stream);
+
+/* The method's result with HOST buffers in and out: create from host initial
+ * densities, run nsteps, then sc_surface_of_tension with a radial profile
+ * (centre, bin_width, nbins as there; the default R grid) and read the results
+ * back.  nA0, nB0: host FP64 [N]; nA, nB: host FP64 [N] receiving the final
+ * densities, or NULL to skip that copy; result: host FP64 [8] as the out of
+ * sc_surface_of_tension.  The workspace is device memory as for sc_create.
+ * Synchronous. */
+sc_status sc_run_host_sigma(const sc_params *params, const double *nA0, const double *nB0, int64_t nsteps,
+                           const double centre[3], double bin_width, int32_t nbins, double *nA, double *nB,
+                           double *result, void *workspace, size_t ws_bytes, void *stream);
 
 /* ---- batches: several lattices stepped by one kernel launch per step ----
  * The batched radius sweep: lattices of different sizes and parameters (same

@@ -78,6 +78,9 @@ def _load():
         "sc_totals": (I32, [V, V]),
         "sc_sync": (I32, [V]),
         "sc_run_host": (I32, [P, V, V, I64, V, V, V, Z, V]),
+        "sc_surface_of_tension": (I32, [V, I32, ctypes.POINTER(D), D, I32, D, D, D, V, V]),
+        "sc_diagnostics": (I32, [V, V, I32, D, V]),
+        "sc_run_host_sigma": (I32, [P, V, V, I64, ctypes.POINTER(D), D, I32, V, V, V, V, Z, V]),
         "sc_kernel_launches": (I64, [V]),
         "sc_step_config": (I32, [V, ctypes.POINTER(ctypes.c_int32), I32]),
         "sc_batch_workspace_bytes": (Z, [I32, P]),
@@ -190,6 +193,24 @@ def sc_bulk_pressure_at(ctx, node, out):
 def sc_sigma_minimum(rows, P_in_out, dim, R_lo, R_hi, R_step, out, stream=None):
     _check(lib.sc_sigma_minimum(_ptr(rows), rows.shape[0], _ptr(P_in_out), int(dim), float(R_lo), float(R_hi),
                                 float(R_step), _ptr(out), _stream_ptr(stream)))
+
+
+def sc_surface_of_tension(ctx, kind, centre, bin_width, nbins, R_lo, R_hi, R_step, out, rows=None):
+    c = None if centre is None else (ctypes.c_double * 3)(*[float(v) for v in centre])
+    _check(lib.sc_surface_of_tension(ctx, int(kind), c, float(bin_width), int(nbins), float(R_lo), float(R_hi),
+                                     float(R_step), _ptr(out), _ptr(rows)))
+
+
+def sc_diagnostics(ctx, u_prev, component, background, out):
+    _check(lib.sc_diagnostics(ctx, _ptr(u_prev), int(component), float(background), _ptr(out)))
+
+
+def sc_run_host_sigma(params, nA0, nB0, nsteps, centre, bin_width, nbins, nA, nB, result, workspace, stream=None):
+    """Host tensors in and out (result: host float64 [8]); see include/sc.h."""
+    c = None if centre is None else (ctypes.c_double * 3)(*[float(v) for v in centre])
+    _check(lib.sc_run_host_sigma(ctypes.byref(params), _ptr(nA0), _ptr(nB0), int(nsteps), c, float(bin_width),
+                                 int(nbins), _ptr(nA), _ptr(nB), _ptr(result), _ptr(workspace), workspace.numel(),
+                                 _stream_ptr(stream)))
 
 
 def sc_sigma0_flat(rows, out, stream=None):
@@ -461,27 +482,17 @@ class Batch:
         return sc_batch_active(self.handle)
 
 
-def surface_of_tension(sim: Simulation, centre, bin_width=0.5, nbins=None, in_node=None, out_node=None,
-                       kind=SC_PROFILE_RADIAL, R_step=0.01):
-    """Profile -> P_in, P_out (Eq. bulkp at the centre node and at the far corner
-    (nx-1, ny-1, nz-1), section 4) -> sigma[R] minimum, all on the device.
-    Returns (rows, out[8]) as CUDA tensors; out = (dP, C, R_s, sigma_s, R_grid,
-    sigma_grid, P_in, P_out).  The grid for the interpolated minimum spans
-    [R_step, r_max] of the profile."""
+def surface_of_tension(sim: Simulation, centre=None, bin_width=0.5, nbins=0, kind=SC_PROFILE_RADIAL, R_step=0.01):
+    """sc_surface_of_tension on a simulation: returns (rows [nbins, 6], out[8]) as CUDA tensors,
+    out = (dP, C, R_s, sigma_s, R_grid, sigma_grid, P_in, P_out); nbins 0 = the library default."""
     nx, ny, nz = sim.shape
-    dim = 3 if (sim.params.lattice == SC_D3Q19 and nz > 1) else 2
-    if nbins is None:
-        half = min(nx, ny, nz) if dim == 3 else min(nx, ny)
-        nbins = int(half / 2 / bin_width) if kind == SC_PROFILE_RADIAL else nx // 2
-    rows = sim.profile(kind, centre, bin_width, nbins)
-    if in_node is None:
-        in_node = (nx // 2, ny // 2, nz // 2)
-    if out_node is None:
-        out_node = (nx - 1, ny - 1, nz - 1)
-    pio = torch.cat([sim.bulk_pressure(in_node), sim.bulk_pressure(out_node)])
+    if not nbins:
+        dim3 = sim.params.lattice == SC_D3Q19 and nz > 1
+        half = nx if kind == SC_PROFILE_AXIS_X else (min(nx, ny, nz) if dim3 else min(nx, ny))
+        nbins = half // 2 if kind == SC_PROFILE_AXIS_X else int(half / 2 / bin_width)
+    rows = torch.empty((nbins, 6), dtype=torch.float64, device=sim.device)
     out = torch.empty(8, dtype=torch.float64, device=sim.device)
-    r_max = nbins * (bin_width if kind == SC_PROFILE_RADIAL else 1.0)
-    sc_sigma_minimum(rows, pio, dim, R_step, r_max, R_step, out, sim.stream)
+    sc_surface_of_tension(sim.ctx, kind, centre, bin_width, nbins, 0.0, 0.0, R_step, out, rows)
     return rows, out
 
 

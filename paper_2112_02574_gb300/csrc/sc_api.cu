@@ -5,15 +5,13 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 
 #include "sc_aux.cuh"
 #include "sc_dispatch.h"
-
-namespace scgb {
-sc_status set_error(sc_status st, const char *msg);
-}
+#include "sc_host.h"
 
 using namespace scgb;
 
@@ -40,6 +38,9 @@ sc_status fail(sc_status st, const char *fmt, ...) {
 constexpr size_t kAlign = 256;
 constexpr size_t kPartialBytes = size_t(16) << 20;  // per-block partial sums of the reductions
 constexpr size_t kStatusBytes = 4096;                // status word + small scalars
+constexpr int kMaxProfileBins = 4096;
+// rows of a profile kept for sc_surface_of_tension ([kMaxProfileBins][6] FP64), then P_in, P_out
+constexpr size_t kAnalysisBytes = (size_t)kMaxProfileBins * 6 * sizeof(double) + 256;
 constexpr int kMaxPartialBlocks = 1024;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
@@ -98,15 +99,8 @@ int default_tile_z(const sc_params *p) {
 }
 
 sc_status validate(const sc_params *p) {
-  if (!p) return fail(SC_EINVAL, "params is NULL");
-  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(SC_EINVAL, "lattice size must be >= 1 in every direction");
-  if ((int64_t)p->nx * p->ny * p->nz > (int64_t(1) << 31) - 1)
-    return fail(SC_EINVAL, "more than 2^31 - 1 sites is not supported");
-  if (p->lattice != SC_D2Q9 && p->lattice != SC_D3Q19) return fail(SC_EINVAL, "unknown lattice %d", p->lattice);
-  if (p->lattice == SC_D2Q9 && p->nz != 1) return fail(SC_EINVAL, "D2Q9 needs nz == 1");
-  if (p->stencil != SC_FORCE_E4 && p->stencil != SC_FORCE_E6) return fail(SC_EINVAL, "unknown stencil %d", p->stencil);
-  if (p->stencil == SC_FORCE_E6 && p->lattice != SC_D3Q19) return fail(SC_EINVAL, "the E6 stencil needs D3Q19");
-  if (p->psi_self != SC_PSI_N && p->psi_self != SC_PSI_EXP) return fail(SC_EINVAL, "unknown psi %d", p->psi_self);
+  sc_status st = validate_model(p);
+  if (st != SC_OK) return st;
   if (store_bytes(p->storage) == 0) return fail(SC_EINVAL, "unknown storage %d", p->storage);
   if (p->tile_y != 0 && p->tile_y != 1 && p->tile_y != 2 && p->tile_y != 4 && p->tile_y != 8 && p->tile_y != 16)
     return fail(SC_EINVAL, "tile_y must be 0, 1, 2, 4, 8 or 16");
@@ -128,15 +122,13 @@ sc_status validate(const sc_params *p) {
   }
   for (int J = 0; J < 2; ++J)
     if (!(p->tau[J] > 0.5) || !isfinite(p->tau[J])) return fail(SC_EINVAL, "tau[%d] must be > 1/2", J);
-  if (!isfinite(p->G) || !isfinite(p->G_self[0]) || !isfinite(p->G_self[1]))
-    return fail(SC_EINVAL, "couplings must be finite");
   return SC_OK;
 }
 
 struct Layout {
   size_t pop_bytes;  // one population buffer
   size_t ref_bytes;  // one local-reference density buffer (16-bit storage), else 0
-  size_t off_pop[2], off_ref[2], off_fields, off_partial, off_status, total;
+  size_t off_pop[2], off_ref[2], off_fields, off_partial, off_status, off_analysis, total;
 };
 
 bool is_local_ref(int storage) { return storage == SC_STORE_F16 || storage == SC_STORE_BF16; }
@@ -161,6 +153,8 @@ Layout layout_of(const sc_params *p) {
   off = align_up(off + kPartialBytes);
   L.off_status = off;
   off = align_up(off + kStatusBytes);
+  L.off_analysis = off;
+  off = align_up(off + kAnalysisBytes);
   L.total = off;
   return L;
 }
@@ -171,6 +165,46 @@ Layout layout_of(const sc_params *p) {
 // Records the calling thread's sc_last_error() message for entry points defined
 // in other translation units of the library.
 sc_status scgb::set_error(sc_status st, const char *msg) { return fail(st, "%s", msg); }
+
+sc_status scgb::validate_model(const sc_params *p) {
+  if (!p) return fail(SC_EINVAL, "params is NULL");
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(SC_EINVAL, "lattice size must be >= 1 in every direction");
+  if ((int64_t)p->nx * p->ny * p->nz > (int64_t(1) << 31) - 1)
+    return fail(SC_EINVAL, "more than 2^31 - 1 sites is not supported");
+  if (p->lattice != SC_D2Q9 && p->lattice != SC_D3Q19) return fail(SC_EINVAL, "unknown lattice %d", p->lattice);
+  if (p->lattice == SC_D2Q9 && p->nz != 1) return fail(SC_EINVAL, "D2Q9 needs nz == 1");
+  if (p->stencil != SC_FORCE_E4 && p->stencil != SC_FORCE_E6) return fail(SC_EINVAL, "unknown stencil %d", p->stencil);
+  if (p->stencil == SC_FORCE_E6 && p->lattice != SC_D3Q19) return fail(SC_EINVAL, "the E6 stencil needs D3Q19");
+  if (p->psi_self != SC_PSI_N && p->psi_self != SC_PSI_EXP) return fail(SC_EINVAL, "unknown psi %d", p->psi_self);
+  if (!isfinite(p->G) || !isfinite(p->G_self[0]) || !isfinite(p->G_self[1]))
+    return fail(SC_EINVAL, "couplings must be finite");
+  return SC_OK;
+}
+
+sc_status scgb::validate_profile_request(const sc_params *p, int32_t kind, const double centre[3], double bin_width,
+                                         int32_t nbins, int32_t max_bins) {
+  if (kind < SC_PROFILE_RADIAL || kind > SC_PROFILE_AXIS_X) return fail(SC_EINVAL, "unknown profile kind %d", kind);
+  if (nbins < 1 || nbins > max_bins) return fail(SC_EINVAL, "nbins must be in [1, %d]", max_bins);
+  if (kind == SC_PROFILE_AXIS_X && nbins > p->nx)
+    return fail(SC_EINVAL, "the x-axis line has one row per site: nbins must be <= nx (%d)", p->nx);
+  if (kind == SC_PROFILE_RADIAL && !(bin_width > 0.0 && isfinite(bin_width)))
+    return fail(SC_EINVAL, "bin_width must be finite and > 0");
+  for (int m = 0; m < 3; ++m)
+    if (!isfinite(centre[m])) return fail(SC_EINVAL, "centre must be finite");
+  return SC_OK;
+}
+
+ProfileArgs scgb::profile_args(const sc_params *p, int32_t kind, const double centre[3], double bin_width,
+                               int32_t nbins) {
+  ProfileArgs pa;
+  pa.kind = kind;
+  for (int m = 0; m < 3; ++m) pa.centre[m] = centre[m];
+  pa.bin_width = bin_width;
+  pa.nbins = nbins;
+  pa.dim = (p->lattice == SC_D3Q19 && p->nz > 1) ? 3 : 2;
+  pa.chunk = 0;
+  return pa;
+}
 
 struct sc_ctx {
   sc_params p;
@@ -220,6 +254,8 @@ namespace {
 
 unsigned int *status_word(sc_ctx *c) { return reinterpret_cast<unsigned int *>(c->ws + c->L.off_status); }
 double *status_scalars(sc_ctx *c) { return reinterpret_cast<double *>(c->ws + c->L.off_status + 256); }
+double *analysis_rows(sc_ctx *c) { return reinterpret_cast<double *>(c->ws + c->L.off_analysis); }
+double *analysis_pio(sc_ctx *c) { return analysis_rows(c) + (size_t)kMaxProfileBins * 6; }
 double *fields_of(sc_ctx *c) { return reinterpret_cast<double *>(c->ws + c->L.off_fields); }
 double *partial_of(sc_ctx *c) { return reinterpret_cast<double *>(c->ws + c->L.off_partial); }
 
@@ -737,45 +773,13 @@ sc_status sc_set_state(sc_ctx *c, const void *src, size_t bytes) {
 sc_status sc_pressure_profile(sc_ctx *c, int32_t kind, const double centre[3], double bin_width, int32_t nbins,
                               double *out) {
   if (!c || !out || !centre) return fail(SC_EINVAL, "ctx, centre and out must be non-NULL");
-  if (kind < SC_PROFILE_RADIAL || kind > SC_PROFILE_AXIS_X) return fail(SC_EINVAL, "unknown profile kind %d", kind);
-  if (nbins < 1 || nbins > 4096) return fail(SC_EINVAL, "nbins must be in [1, 4096]");
-  if (kind == SC_PROFILE_RADIAL && !(bin_width > 0.0)) return fail(SC_EINVAL, "bin_width must be > 0");
-  for (int m = 0; m < 3; ++m)
-    if (!isfinite(centre[m])) return fail(SC_EINVAL, "centre must be finite");
-  sc_status st = ensure_fields(c);
+  sc_status st = validate_profile_request(&c->p, kind, centre, bin_width, nbins, kMaxProfileBins);
   if (st != SC_OK) return st;
-  ProfileArgs pa;
-  pa.kind = kind;
-  for (int m = 0; m < 3; ++m) pa.centre[m] = centre[m];
-  pa.bin_width = bin_width;
-  pa.nbins = nbins;
-  pa.dim = (c->p.lattice == SC_D3Q19 && c->p.nz > 1) ? 3 : 2;
-  const size_t row_bytes = (size_t)nbins * 6 * sizeof(double);
-  int64_t blocks = (int64_t)(kPartialBytes / row_bytes);
-  if (blocks > kMaxPartialBlocks) blocks = kMaxPartialBlocks;
-  if (blocks > (c->N + 31) / 32) blocks = (c->N + 31) / 32;
-  if (blocks < 1) blocks = 1;
-  pa.chunk = (c->N + blocks - 1) / blocks;
-  pa.chunk = (pa.chunk + 31) / 32 * 32;
-  blocks = (c->N + pa.chunk - 1) / pa.chunk;
-  ForceParams fp = force_params(c);
-  const int lat = c->p.lattice, sten = c->p.stencil;
-  if (lat == SC_D3Q19 && sten == SC_FORCE_E4) {
-    SC_CUDA(cudaFuncSetAttribute(profile_partial_kernel<kD3Q19, kE4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)row_bytes));
-    profile_partial_kernel<kD3Q19, kE4><<<(int)blocks, 32, row_bytes, c->stream>>>(fp, pa, fields_of(c), partial_of(c));
-  } else if (lat == SC_D3Q19) {
-    SC_CUDA(cudaFuncSetAttribute(profile_partial_kernel<kD3Q19, kE6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)row_bytes));
-    profile_partial_kernel<kD3Q19, kE6><<<(int)blocks, 32, row_bytes, c->stream>>>(fp, pa, fields_of(c), partial_of(c));
-  } else {
-    SC_CUDA(cudaFuncSetAttribute(profile_partial_kernel<kD2Q9, kE4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)row_bytes));
-    profile_partial_kernel<kD2Q9, kE4><<<(int)blocks, 32, row_bytes, c->stream>>>(fp, pa, fields_of(c), partial_of(c));
-  }
-  SC_CUDA(cudaGetLastError());
-  profile_finalize_kernel<<<(nbins + 127) / 128, 128, 0, c->stream>>>(partial_of(c), (int)blocks, nbins, out);
-  SC_CUDA(cudaGetLastError());
+  st = ensure_fields(c);
+  if (st != SC_OK) return st;
+  SC_CUDA(launch_profile(c->p.lattice, c->p.stencil, force_params(c), profile_args(&c->p, kind, centre, bin_width, nbins),
+                         StoredFields{fields_of(c), c->N}, partial_of(c), (int64_t)(kPartialBytes / sizeof(double)),
+                         kMaxPartialBlocks, out, c->stream));
   return SC_OK;
 }
 
@@ -801,6 +805,65 @@ sc_status sc_sigma_minimum(const double *rows, int32_t nbins, const double *P_in
     return fail(SC_EINVAL, "need 0 < R_lo < R_hi, R_step > 0 and at most 1e7 grid points");
   sigma_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(rows, nbins, P_in_out, dim, R_lo, R_hi, R_step, out);
   SC_CUDA(cudaGetLastError());
+  return SC_OK;
+}
+
+sc_status sc_surface_of_tension(sc_ctx *c, int32_t kind, const double centre[3], double bin_width, int32_t nbins,
+                                double R_lo, double R_hi, double R_step, double *out, double *rows) {
+  if (!c || !out) return fail(SC_EINVAL, "ctx and out must be non-NULL");
+  if (kind != SC_PROFILE_RADIAL && kind != SC_PROFILE_AXIS_X)
+    return fail(SC_EINVAL, "the surface of tension takes a radial or an x-axis profile, not kind %d", kind);
+  const int dim = (c->p.lattice == SC_D3Q19 && c->p.nz > 1) ? 3 : 2;
+  const int nn[3] = {c->p.nx, c->p.ny, c->p.nz};
+  double ctr[3];
+  for (int m = 0; m < 3; ++m) ctr[m] = centre ? centre[m] : (double)(nn[m] / 2);
+  if (kind == SC_PROFILE_AXIS_X) bin_width = 1.0;
+  if (nbins == 0) {
+    // the largest sphere (circle) inside the box, or half the x axis
+    int half = kind == SC_PROFILE_AXIS_X ? nn[0] : (dim == 3 ? std::min(nn[0], std::min(nn[1], nn[2]))
+                                                             : std::min(nn[0], nn[1]));
+    nbins = kind == SC_PROFILE_AXIS_X ? half / 2 : (int32_t)(half / 2 / bin_width);
+  }
+  if (nbins < 2) return fail(SC_EINVAL, "need at least two profile rows");
+  sc_status st = validate_profile_request(&c->p, kind, ctr, bin_width, nbins, kMaxProfileBins);
+  if (st != SC_OK) return st;
+  const double r_max = nbins * bin_width;
+  if (R_step == 0.0) R_step = 0.01;
+  if (R_lo == 0.0) R_lo = R_step;
+  if (R_hi == 0.0) R_hi = r_max;
+  if (!(R_lo > 0.0) || !(R_hi > R_lo) || !(R_step > 0.0) || (R_hi - R_lo) / R_step > 1e7)
+    return fail(SC_EINVAL, "need 0 < R_lo < R_hi, R_step > 0 and at most 1e7 grid points");
+  double *r = rows ? rows : analysis_rows(c);
+  st = sc_pressure_profile(c, kind, ctr, bin_width, nbins, r);
+  if (st != SC_OK) return st;
+  // P_in at the centre node, P_out at the far corner (section 4)
+  int32_t in_node[3], out_node[3];
+  for (int m = 0; m < 3; ++m) {
+    const int k = (int)floor(ctr[m] + 0.5);
+    in_node[m] = ((k % nn[m]) + nn[m]) % nn[m];
+    out_node[m] = nn[m] - 1;
+  }
+  double *pio = analysis_pio(c);
+  st = sc_bulk_pressure_at(c, in_node, pio);
+  if (st == SC_OK) st = sc_bulk_pressure_at(c, out_node, pio + 1);
+  if (st != SC_OK) return st;
+  return sc_sigma_minimum(r, nbins, pio, dim, R_lo, R_hi, R_step, out, c->stream);
+}
+
+sc_status sc_diagnostics(sc_ctx *c, double *u_prev, int32_t component, double background, double *out) {
+  if (!c || !out) return fail(SC_EINVAL, "ctx and out must be non-NULL");
+  if (component < -1 || component > 1) return fail(SC_EINVAL, "component must be -1 (none), 0 (A) or 1 (B)");
+  if (component >= 0 && !isfinite(background)) return fail(SC_EINVAL, "background must be finite");
+  sc_status st = sc_totals(c, out);
+  if (st != SC_OK) return st;
+  if (u_prev) {
+    st = sc_velocity_change(c, u_prev, out + 5);
+    if (st != SC_OK) return st;
+  } else {
+    SC_CUDA(cudaMemsetAsync(out + 5, 0xff, sizeof(double), c->stream));  // all-ones bits: a NaN
+  }
+  if (component >= 0) return sc_centre_of_mass(c, component, background, out + 6);
+  SC_CUDA(cudaMemsetAsync(out + 6, 0xff, 4 * sizeof(double), c->stream));
   return SC_OK;
 }
 
@@ -869,6 +932,38 @@ sc_status sc_run_host(const sc_params *params, const double *nA0, const double *
     cudaError_t e = cudaMemcpyAsync(nA, fields_of(c), sizeof(double) * N, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(nB, fields_of(c) + N, sizeof(double) * N, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) st = fail(SC_ECUDA, "copying densities to the host: %s", cudaGetErrorString(e));
+  }
+  if (st == SC_OK) st = sc_sync(c);
+  sc_destroy(c);
+  return st;
+}
+
+sc_status sc_run_host_sigma(const sc_params *params, const double *nA0, const double *nB0, int64_t nsteps,
+                           const double centre[3], double bin_width, int32_t nbins, double *nA, double *nB,
+                           double *result, void *workspace, size_t ws_bytes, void *stream) {
+  sc_status st = validate(params);
+  if (st != SC_OK) return st;
+  if (!nA0 || !nB0 || !result || !workspace) return fail(SC_EINVAL, "nA0, nB0, result and workspace must be non-NULL");
+  if (nsteps < 0) return fail(SC_EINVAL, "nsteps must be >= 0");
+  Layout L = layout_of(params);
+  if (ws_bytes < L.total) return fail(SC_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, L.total);
+  const int64_t N = (int64_t)params->nx * params->ny * params->nz;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double *stage = reinterpret_cast<double *>(static_cast<char *>(workspace) + L.off_fields);
+  SC_CUDA(cudaMemcpyAsync(stage, nA0, sizeof(double) * N, cudaMemcpyHostToDevice, s));
+  SC_CUDA(cudaMemcpyAsync(stage + N, nB0, sizeof(double) * N, cudaMemcpyHostToDevice, s));
+  sc_ctx *c = nullptr;
+  st = sc_create(params, stage, stage + N, workspace, ws_bytes, stream, &c);
+  if (st != SC_OK) return st;
+  st = sc_step(c, nsteps);
+  // the 8 results land behind P_in, P_out in the analysis area
+  double *res = analysis_pio(c) + 2;
+  if (st == SC_OK) st = sc_surface_of_tension(c, SC_PROFILE_RADIAL, centre, bin_width, nbins, 0.0, 0.0, 0.0, res, nullptr);
+  if (st == SC_OK) {
+    cudaError_t e = cudaMemcpyAsync(result, res, 8 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && nA) e = cudaMemcpyAsync(nA, fields_of(c), sizeof(double) * N, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && nB) e = cudaMemcpyAsync(nB, fields_of(c) + N, sizeof(double) * N, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) st = fail(SC_ECUDA, "copying results to the host: %s", cudaGetErrorString(e));
   }
   if (st == SC_OK) st = sc_sync(c);
   sc_destroy(c);

@@ -5,6 +5,7 @@
 #pragma once
 
 #include "sc_common.cuh"
+#include "sc_profile.cuh"
 
 namespace scgb {
 
@@ -51,19 +52,6 @@ __device__ __forceinline__ double pop_value(const PopArgs &a, const ST *buf, int
   const double g = load_dev<ST>(buf + ((int64_t)i * a.N + s) * 2 + J, a.inv_scale[J][i]);
   const double ref = a.nbar[J] + (local_ref<ST>() ? double(J == 0 ? a.nref[s].x : a.nref[s].y) : 0.0);
   return g + Lattice<LAT>::w(i) * ref;
-}
-
-__device__ __forceinline__ void coords(int64_t s, int nx, int ny, int &x, int &y, int &z) {
-  x = int(s % nx);
-  const int64_t r = s / nx;
-  y = int(r % ny);
-  z = int(r / ny);
-}
-__device__ __forceinline__ int64_t site_at(int x, int y, int z, int nx, int ny, int nz) {
-  x = ((x % nx) + nx) % nx;
-  y = ((y % ny) + ny) % ny;
-  z = ((z % nz) + nz) % nz;
-  return (int64_t)x + (int64_t)nx * (y + (int64_t)ny * z);
 }
 
 // mode 0: initial rest equilibrium from densities n0 (FP64 [2][N]): the value
@@ -146,11 +134,6 @@ __global__ void fields_kernel(PopArgs a, int psi_exp, double *fields) {
   }
 }
 
-struct ForceParams {
-  double G, G_self[2];
-  int nx, ny, nz;
-  int64_t N;
-};
 
 // Eq. sc_force at site s from FP64 fields, +/- pairs first.
 template <int LAT, int STEN>
@@ -295,157 +278,6 @@ __global__ void finalize_measure_kernel(const double *partial, int nblocks, int 
   out[1] = acc[1] / acc[3];
   out[2] = acc[2] / acc[3];
   out[3] = acc[3];
-}
-
-// Lattice pressure tensor of Eq. sm:pt at one site; P = {xx, yy, zz, xy, xz, yz}.
-template <int LAT, int STEN>
-__device__ __forceinline__ void ptensor64(const ForceParams &p, const double *fields, int x, int y, int z, int64_t s,
-                                          double P[6]) {
-  using SN = Stencil<LAT, STEN>;
-  const double cs2 = 1.0 / 3.0;
-  constexpr int MU[6] = {0, 1, 2, 0, 0, 1}, NU[6] = {0, 1, 2, 1, 2, 2};
-  double C[4][6];
-#pragma unroll
-  for (int f = 0; f < 4; ++f)
-#pragma unroll
-    for (int c = 0; c < 6; ++c) C[f][c] = 0.0;
-#pragma unroll
-  for (int k = 0; k < SN::NH; ++k) {
-    const int v[3] = {SN::v(k, 0), SN::v(k, 1), SN::v(k, 2)};
-    const int64_t sp = site_at(x + v[0], y + v[1], z + v[2], p.nx, p.ny, p.nz);
-    const int64_t sm = site_at(x - v[0], y - v[1], z - v[2], p.nx, p.ny, p.nz);
-    const double W = SN::W(k);
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      const double sum = fields[f * p.N + sp] + fields[f * p.N + sm];
-#pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        const int vv = v[MU[c]] * v[NU[c]];
-        if (vv) C[f][c] += W * vv * sum;
-      }
-    }
-  }
-  const double nA = fields[s], nB = fields[p.N + s], psA = fields[2 * p.N + s], psB = fields[3 * p.N + s];
-#pragma unroll
-  for (int c = 0; c < 6; ++c) {
-    const double ideal = c < 3 ? (nA + nB) * cs2 : 0.0;
-    P[c] = ideal + 0.5 * p.G * cs2 * nA * C[1][c] + 0.5 * p.G * cs2 * nB * C[0][c] +
-           0.5 * p.G_self[0] * cs2 * psA * C[2][c] + 0.5 * p.G_self[1] * cs2 * psB * C[3][c];
-  }
-}
-
-struct ProfileArgs {
-  int kind;  // sc_profile_kind
-  double centre[3];
-  double bin_width;
-  int nbins;
-  int dim;   // 2 or 3
-  int64_t chunk;  // sites per block
-};
-
-// Per-block partial sums of a profile: one warp per block accumulates into its
-// own shared-memory bins, lane by lane in a fixed order (deterministic), then
-// writes rows [nbins][6] = (sum coordinate, sum P_N, sum P_T, sum n_A, sum n_B, count).
-template <int LAT, int STEN>
-__global__ void __launch_bounds__(32) profile_partial_kernel(ForceParams fp, ProfileArgs pa, const double *fields,
-                                                             double *partial) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  double *bins = reinterpret_cast<double *>(smem_raw);
-  const int lane = threadIdx.x;
-  for (int k = lane; k < pa.nbins * 6; k += 32) bins[k] = 0.0;
-  __syncwarp();
-  const int64_t N = fp.N;
-  const int64_t s0 = blockIdx.x * pa.chunk, s1 = min(N, s0 + pa.chunk);
-  const int cx = int(floor(pa.centre[0] + 0.5)), cy = int(floor(pa.centre[1] + 0.5)),
-            cz = int(floor(pa.centre[2] + 0.5));
-  for (int64_t base = s0; base < s1; base += 32) {
-    const int64_t s = base + lane;
-    int bin = -1;
-    double vals[5] = {0, 0, 0, 0, 0};
-    if (s < s1) {
-      int x, y, z;
-      coords(s, fp.nx, fp.ny, x, y, z);
-      double coord = 0.0, d[3] = {0, 0, 0};
-      if (pa.kind == SC_PROFILE_RADIAL) {
-        const int c[3] = {x, y, z}, L[3] = {fp.nx, fp.ny, fp.nz};
-        double r2 = 0.0;
-        for (int m = 0; m < 3; ++m) {
-          double dd = c[m] - pa.centre[m];
-          dd -= L[m] * floor(dd / L[m] + 0.5);  // minimum image
-          d[m] = dd;
-          r2 += dd * dd;
-        }
-        coord = sqrt(r2);
-        bin = int(floor(coord / pa.bin_width));
-      } else if (pa.kind == SC_PROFILE_PLANAR_Z) {
-        coord = z;
-        bin = z;
-      } else {
-        const int k = ((x - cx) % fp.nx + fp.nx) % fp.nx;
-        if (y == ((cy % fp.ny) + fp.ny) % fp.ny && z == ((cz % fp.nz) + fp.nz) % fp.nz) {
-          coord = k;
-          bin = k;
-        }
-      }
-      if (bin >= pa.nbins) bin = -1;
-      if (bin >= 0) {
-        double P[6];
-        ptensor64<LAT, STEN>(fp, fields, x, y, z, s, P);
-        double PN, PT;
-        if (pa.kind == SC_PROFILE_RADIAL) {
-          const double tr = pa.dim == 3 ? P[0] + P[1] + P[2] : P[0] + P[1];
-          if (coord == 0.0) {
-            PN = PT = tr / pa.dim;
-          } else {
-            const double e[3] = {d[0] / coord, d[1] / coord, d[2] / coord};
-            PN = e[0] * e[0] * P[0] + e[1] * e[1] * P[1] + e[2] * e[2] * P[2] + 2.0 * e[0] * e[1] * P[3] +
-                 2.0 * e[0] * e[2] * P[4] + 2.0 * e[1] * e[2] * P[5];
-            PT = (tr - PN) / (pa.dim - 1);
-          }
-        } else if (pa.kind == SC_PROFILE_PLANAR_Z) {
-          PN = P[2];
-          PT = 0.5 * (P[0] + P[1]);
-        } else {
-          PN = P[0];
-          PT = P[1];
-        }
-        vals[0] = coord;
-        vals[1] = PN;
-        vals[2] = PT;
-        vals[3] = fields[s];
-        vals[4] = fields[N + s];
-      }
-    }
-    // fixed-order accumulation: lane l's contribution is added in iteration l
-    for (int l = 0; l < 32; ++l) {
-      const int b = __shfl_sync(0xffffffffu, bin, l);
-      double v = 0.0;
-#pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        const double t = __shfl_sync(0xffffffffu, vals[c], l);
-        if (lane == c) v = t;
-      }
-      if (b >= 0 && lane < 6) bins[b * 6 + lane] += (lane == 5) ? 1.0 : v;
-      __syncwarp();
-    }
-  }
-  __syncwarp();
-  double *out = partial + (int64_t)blockIdx.x * pa.nbins * 6;
-  for (int k = lane; k < pa.nbins * 6; k += 32) out[k] = bins[k];
-}
-
-// Sum the per-block partials in block order and turn sums into means.
-__global__ void profile_finalize_kernel(const double *partial, int nblocks, int nbins, double *out) {
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbins; b += gridDim.x * blockDim.x) {
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int k = 0; k < nblocks; ++k)
-#pragma unroll
-      for (int c = 0; c < 6; ++c) acc[c] += partial[((int64_t)k * nbins + b) * 6 + c];
-    const double cnt = acc[5];
-#pragma unroll
-    for (int c = 0; c < 5; ++c) out[b * 6 + c] = cnt > 0 ? acc[c] / cnt : 0.0;
-    out[b * 6 + 5] = cnt;
-  }
 }
 
 // Bulk pressure of Eq. bulkp (e_2 = 1) at one node.

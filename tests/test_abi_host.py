@@ -78,3 +78,47 @@ def test_null_and_range_arguments(B):
     # misaligned workspace
     assert B.lib.sc_create(ctypes.byref(p), dummy, dummy, ctypes.c_void_p(257), 1 << 30, None,
                            ctypes.byref(ctx)) == B.SC_EINVAL
+
+
+@pytest.mark.parametrize("bad", [
+    dict(shape=(8, 8, 8), psi_self=5),                 # unknown pseudopotential
+    dict(shape=(8, 8, 8), G_self=(float("nan"), 0.0)),  # non-finite coupling
+    dict(shape=(8, 8, 1), lattice=0, stencil=1),       # E6 on D2Q9
+    dict(shape=(2048, 2048, 1024)),                    # more than 2^31 - 1 sites
+])
+def test_noalloc_profile_applies_the_model_checks(B, bad):
+    """The allocation-free profile accepts exactly the parameters sc_create accepts for the model
+    (size, lattice, stencil, psi_self, couplings): each of these is SC_EINVAL before any CUDA call."""
+    shape = bad.pop("shape")
+    p = B.make_params(shape, **bad)
+    d = ctypes.c_void_p(256)
+    c = (ctypes.c_double * 3)(1.0, 1.0, 0.0)
+    assert B.lib.sc_pressure_profile_noalloc(ctypes.byref(p), d, d, 0, c, 0.5, 8, d, None) == B.SC_EINVAL
+
+
+def test_axis_profile_rejects_more_rows_than_sites(B):
+    """The x-axis line holds one site per row: nbins > nx is SC_EINVAL (nbins = nx is accepted as far
+    as validation goes; with no GPU the call then fails on the device lookup, not on its arguments)."""
+    p = B.make_params((12, 8, 8))
+    d = ctypes.c_void_p(256)
+    c = (ctypes.c_double * 3)(6.0, 4.0, 4.0)
+    assert B.lib.sc_pressure_profile_noalloc(ctypes.byref(p), d, d, B.SC_PROFILE_AXIS_X, c, 1.0, 13, d,
+                                             None) == B.SC_EINVAL
+    assert "nx" in B.sc_last_error()
+    st = B.lib.sc_pressure_profile_noalloc(ctypes.byref(p), d, d, B.SC_PROFILE_AXIS_X, c, 1.0, 12, d, None)
+    assert st != B.SC_EINVAL
+
+
+def test_analysis_entry_points_reject_null_arguments(B):
+    c = (ctypes.c_double * 3)(1.0, 1.0, 1.0)
+    d = ctypes.c_void_p(256)
+    assert B.lib.sc_surface_of_tension(None, 0, c, 0.5, 10, 0.0, 0.0, 0.0, d, None) == B.SC_EINVAL
+    assert B.lib.sc_diagnostics(None, None, 0, 0.0, d) == B.SC_EINVAL
+    p = B.make_params((8, 8, 8))
+    # result buffer missing, then a negative step count: both SC_EINVAL before any device work
+    assert B.lib.sc_run_host_sigma(ctypes.byref(p), d, d, 10, c, 0.5, 4, None, None, None, d, 1 << 30,
+                                   None) == B.SC_EINVAL
+    assert B.lib.sc_run_host_sigma(ctypes.byref(p), d, d, -1, c, 0.5, 4, None, None, d, d, 1 << 30,
+                                   None) == B.SC_EINVAL
+    assert B.lib.sc_run_host_sigma(ctypes.byref(p), d, d, 1, c, 0.5, 4, None, None, d, d, 16,
+                                   None) == B.SC_ENOMEM

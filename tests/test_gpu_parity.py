@@ -6,10 +6,9 @@ Tolerances
   order -> max |f_gpu - f_orc| <= 1e-13 max |f| after the steps run here.
 * FP32 storage (deviations from the rest equilibrium) + FP32 collision:
   densities and populations within 1e-6 relative of the FP64 oracle (max-norm,
-  normalised by the field's max); the velocity within 1e-6 in lattice units
-  (relative to the lattice speed 1): u is a small difference of O(0.1)
-  populations, each stored with an FP32 rounding of ~1e-8, so its error is set
-  by that absolute scale, not by max |u| ~ 1e-2.
+  normalised by the field's max); the velocity within 1e-5 relative to max |u|
+  (FP32_U_REL below: u is a small difference of O(0.1) populations, each
+  stored with an FP32 rounding, so its error is set by that absolute scale).
 * Integer-like results (counts, bitwise symmetries, tile independence in FP64,
   checkpoint/resume) are exact."""
 import numpy as np
@@ -45,6 +44,16 @@ def setup(B, shape, storage, lattice=1, stencil=0, psi=1, tau=(1.0, 0.9), G=2.5,
                       G_self=G_self, tile_y=tile_y, tile_z=tile_z)
     op = oracle.Params(shape=shape, lattice=lattice, stencil=stencil, psi_self=psi, tau=tau, G=G, G_self=G_self)
     return B.Simulation(p, nA0, nB0), op, nA0, nB0
+
+
+# FP32 storage: the common velocity of Eq. u relative to max|u|.  u is a difference of populations of
+# order w_i n ~ 0.03-0.3, each stored in FP32 as a deviation of up to M ~ 0.45 w_1 (the interface) and
+# rounded once per step (relative 2^-24), with a few more FP32 roundings of the same size in the
+# collision; after k steps the ~20 populations entering u carry independent errors of about
+# sqrt(k) 4 ulp(M) ~ 3.5 x 4 x 1.5e-9 = 2e-8 each, so |du| ~ sqrt(20) x 2e-8 ~ 1e-7 in lattice units,
+# i.e. 1e-5 relative to max|u| ~ 1e-2 (measured over the cases here: 0.8e-6 .. 4.5e-6).  The 1e-6 of
+# the densities and populations cannot hold for u, a small difference of large terms.
+FP32_U_REL = 1e-5
 
 
 def rel(a, b):
@@ -89,7 +98,9 @@ def test_fp32_step_matches_oracle(B, shape, lattice, stencil, psi, G_self):
     nA, nB, u = sim.moments()
     oA, oB, ou = oracle.moments(op, ref)
     assert rel(nA.cpu(), oA) < 1e-6 and rel(nB.cpu(), oB) < 1e-6
-    assert np.abs(u.cpu().numpy() - ou).max() < 1e-6
+    eu = rel(u.cpu().numpy(), ou)  # max |u_gpu - u_orc| / max |u_orc|
+    print(f"FP32 storage, 12 steps: u within {eu:.2e} of max|u| = {np.abs(ou).max():.2e}")
+    assert eu < FP32_U_REL
     assert rel(sim.populations().cpu().numpy(), ref) < 1e-6
 
 
@@ -514,3 +525,124 @@ def test_step_graph_replay_equals_plain_launches(B):
         b.step(1)
     np.testing.assert_array_equal(a.state().cpu().numpy(), b.state().cpu().numpy())
     assert a.launches == 74 and b.launches == 74
+
+
+@pytest.mark.parametrize("kind", ["RADIAL", "AXIS_X"])
+def test_surface_of_tension_matches_oracle(B, kind):
+    """sc_surface_of_tension in one call (section 3: Eqs. gen_sigma, gen_d_sigma and the minimum;
+    section 4: P_in at the centre node, P_out at the far corner) against the oracle's profile, Eq.
+    bulkp at those nodes and the oracle's closed-form and grid minima, FP64 storage."""
+    import torch
+
+    import oracle.sigma as SG
+
+    shape = (36, 34, 38)
+    sim, op, nA0, nB0 = setup(B, shape, B.SC_STORE_F64, 1, 0, 1, G=3.6, G_self=(-0.6, 0.0), amp=1e-2, radius=8.0,
+                              n_in=0.95, n_out=0.05)
+    sim.step(300)
+    f = sim.populations().cpu().numpy()
+    oA, oB, _ = oracle.moments(op, f, with_u=False)
+    k = getattr(B, f"SC_PROFILE_{kind}")
+    nbins = 34 if kind == "RADIAL" else 18  # min(shape) / 2 / 0.5 and nx / 2
+    out = torch.empty(8, dtype=torch.float64, device="cuda")
+    rows = torch.empty((nbins, 6), dtype=torch.float64, device="cuda")
+    B.sc_surface_of_tension(sim.ctx, k, None, 0.5, 0, 0.0, 0.0, 0.0, out, rows)  # all defaults
+    o = out.cpu().numpy()
+    centre = (18.0, 17.0, 19.0)
+    want_rows = oracle.profile(op, oA, oB, k, centre, 0.5 if kind == "RADIAL" else 1.0, nbins)
+    np.testing.assert_array_equal(rows.cpu().numpy()[:, 5], want_rows[:, 5])
+    np.testing.assert_allclose(rows.cpu().numpy(), want_rows, rtol=1e-12, atol=1e-14)
+    c = 18 + 36 * (17 + 34 * 19)
+    p_in, p_out = oracle.bulk_pressure(op, oA[c], oB[c]), oracle.bulk_pressure(op, oA[-1], oB[-1])
+    r, _, pt, _, _ = SG.clean_profile(want_rows)
+    want = SG.surface_of_tension(r, pt, p_in, p_out)
+    assert want["dP"] > 1e-3 and (kind == "AXIS_X" or 4.0 < want["Rs"] < 12.0)  # a formed droplet
+    assert o[6] == pytest.approx(p_in, rel=1e-13) and o[7] == pytest.approx(p_out, rel=1e-13)
+    for i, key in enumerate(("dP", "C", "Rs", "sigma_s")):
+        assert o[i] == pytest.approx(want[key], rel=1e-12), key
+    r_max = nbins * (0.5 if kind == "RADIAL" else 1.0)
+    Rg, sg = SG.argmin_on_grid(r, pt, p_in, p_out, 0.01, r_max, 0.01)
+    assert o[4] == pytest.approx(Rg, rel=1e-9) and o[5] == pytest.approx(sg, rel=1e-9)
+    # the binding's one-line wrapper gives the same numbers
+    _, o2 = B.surface_of_tension(sim, None, 0.5, kind=k)
+    np.testing.assert_array_equal(o2.cpu().numpy(), o)
+
+
+def test_diagnostics_equals_the_separate_calls(B):
+    """sc_diagnostics = sc_totals, sc_velocity_change and sc_centre_of_mass in one call, bit for bit;
+    NaN where a part is switched off."""
+    import torch
+
+    shape = (40, 24, 20)
+    sim, *_ = setup(B, shape, B.SC_STORE_F32, amp=1e-2)
+    sim.step(5)
+    _, _, u0 = sim.moments()
+    u_a, u_b = u0.clone(), u0.clone()
+    sim.step(4)
+    out = torch.empty(10, dtype=torch.float64, device="cuda")
+    B.sc_diagnostics(sim.ctx, u_a, 0, 0.15, out)
+    tot = sim.totals()
+    du = torch.empty(1, dtype=torch.float64, device="cuda")
+    B.sc_velocity_change(sim.ctx, u_b, du)
+    com = sim.centre_of_mass(0, 0.15)
+    want = torch.cat([tot, du, com]).cpu().numpy()
+    np.testing.assert_array_equal(out.cpu().numpy(), want)
+    np.testing.assert_array_equal(u_a.cpu().numpy(), u_b.cpu().numpy())  # u_prev updated alike
+    B.sc_diagnostics(sim.ctx, None, -1, 0.0, out)
+    o = out.cpu().numpy()
+    np.testing.assert_array_equal(o[:5], tot.cpu().numpy())
+    assert np.isnan(o[5:]).all()
+
+
+def test_run_host_sigma_matches_device_path(B):
+    """The host-buffer entry point returns the densities and (dP, C, R_s, sigma_s, ...) of the same
+    run on the device path, bit for bit."""
+    import torch
+
+    shape = (40, 32, 36)
+    nA0, nB0 = S.droplet(shape[::-1], (20, 16, 18), 7.0, n_in=0.9, n_out=0.1)
+    p = B.make_params(shape, psi_self=1, storage=B.SC_STORE_F32, G=3.6)
+    ws = torch.empty(B.sc_workspace_bytes(p), dtype=torch.uint8, device="cuda")
+    hA = torch.from_numpy(nA0.reshape(-1)).pin_memory()
+    hB = torch.from_numpy(nB0.reshape(-1)).pin_memory()
+    oA, oB = torch.empty_like(hA).pin_memory(), torch.empty_like(hB).pin_memory()
+    res = torch.empty(8, dtype=torch.float64).pin_memory()
+    B.sc_run_host_sigma(p, hA, hB, 70, (20.0, 16.0, 18.0), 0.5, 32, oA, oB, res, ws)
+    sim = B.Simulation(p, nA0, nB0)
+    sim.step(70)
+    _, out = B.surface_of_tension(sim, (20.0, 16.0, 18.0), 0.5, nbins=32)
+    nA, nB, _ = sim.moments(with_u=False)
+    np.testing.assert_array_equal(res.numpy(), out.cpu().numpy())
+    np.testing.assert_array_equal(oA.numpy(), nA.cpu().numpy())
+    np.testing.assert_array_equal(oB.numpy(), nB.cpu().numpy())
+    assert res[0] > 0 and np.isfinite(res.numpy()).all()
+
+
+def test_axis_profile_rejects_more_rows_than_sites(B):
+    sim, *_ = setup(B, (20, 12, 10), B.SC_STORE_F64)
+    with pytest.raises(B.ScError) as e:
+        sim.profile(B.SC_PROFILE_AXIS_X, (10.0, 6.0, 5.0), 1.0, 21)
+    assert e.value.status == B.SC_EINVAL
+    rows = sim.profile(B.SC_PROFILE_AXIS_X, (10.0, 6.0, 5.0), 1.0, 20).cpu().numpy()
+    assert (rows[:, 5] == 1).all()
+
+
+def test_fp64_step_matches_oracle_over_a_convergence_interval(B):
+    """The FP64-storage path, which the reduced-precision errors are measured against, against the
+    oracle over one convergence interval of section 4 (2^11 steps) on a 64^3 droplet with asymmetric
+    couplings and psi = exp(-1/n).  Both sides are FP64 in a different order of operations; each step
+    adds a relative difference of order 2^-52 per value, so after k = 2048 steps the densities are held
+    to 1e-12 relative (k x 2.2e-16 = 4.5e-13) and the velocity, a difference of O(0.1) populations
+    with max|u| ~ 1e-2, to 1e-11 relative to max|u| (1e-13 in lattice units)."""
+    shape = (64, 64, 64)
+    sim, op, nA0, nB0 = setup(B, shape, B.SC_STORE_F64, 1, 0, 1, tau=(1.0, 1.0), G=3.6, G_self=(-0.6, 0.0),
+                              radius=12.0, n_in=0.95, n_out=0.05)
+    sim.step(2048)
+    sim.sync()
+    nA, nB, u = sim.moments()
+    ref = oracle.step(op, oracle.init(op, nA0, nB0), 2048)
+    oA, oB, ou = oracle.moments(op, ref)
+    ea, eb = rel(nA.cpu(), oA), rel(nB.cpu(), oB)
+    eu = float(np.abs(u.cpu().numpy() - ou).max() / np.abs(ou).max())
+    print(f"FP64 storage after 2048 steps at 64^3: n_A {ea:.2e}, n_B {eb:.2e}, u (rel. max|u|) {eu:.2e}")
+    assert ea < 1e-12 and eb < 1e-12 and eu < 1e-11
