@@ -371,6 +371,10 @@ def run_gpu(args, rank, world, local_rank):
     if not args.no_batch and rank == 0:
         batch = batch_block(B, dev, stream, value / world if storage == "f32" else None)
 
+    e6 = None
+    if not args.no_batch and rank == 0:
+        e6 = e6_slab_block(B, dev, stream)
+
     if rank != 0:
         return
     line = {
@@ -387,7 +391,7 @@ def run_gpu(args, rank, world, local_rank):
                          / (kern_ms * 1e-3) / 1e9 / peak} if storage in LOCAL_REF_BYTES else {})},
         "hbm_roofline_mlups_frac": value / world * 1e6 * BYTES_PER_SITE[storage] / (peak * 1e9),
         "gpu_launches": launches, "clocks": clk.summary(), "e2e": e2e, "precision": precision,
-        "batch_sweep": batch,
+        "batch_sweep": batch, "e6_slab": e6,
         "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
     }
     if not args.no_cpu_baseline:
@@ -449,6 +453,38 @@ def batch_block(B, dev, stream, plain_mlups, steps=128):
                      "tuning": [[list(c), round(m, 4)] for c, m in table]}
         del batch
     return res
+
+
+def e6_slab_block(B, dev, stream, steps=1024):
+    """The flat-interface slab workload: D3Q19 64 x 64 x 256, an A-rich band of width 128 along z, the
+    extended (E6) forcing stencil, asymmetric couplings (G_AA c_s^2 = -0.2) with psi = exp(-1/n), FP32
+    storage.  Fused steps timed with CUDA events on the launching stream; roofline on the 304-B
+    algorithmic bytes per site update of the step kernel (the generic kernel: E6 reaches two sites)."""
+    import torch
+
+    import sc_synth
+
+    shape = (64, 64, 256)
+    nA0, nB0 = sc_synth.slab(shape[::-1], 128.0, amplitude=1e-3)
+    params = B.make_params(shape, lattice=B.SC_D3Q19, stencil=B.SC_FORCE_E6, psi_self=B.SC_PSI_EXP,
+                           storage=B.SC_STORE_F32, G=G_CROSS, G_self=(-0.6, 0.0))
+    with torch.cuda.stream(stream):
+        sim = B.Simulation(params, nA0, nB0, device=dev, stream=stream)
+        B.sc_step(sim.ctx, 128)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        B.sc_step(sim.ctx, steps)
+        b.record(stream)
+        b.synchronize()
+        B.sc_sync(sim.ctx)
+    ms = a.elapsed_time(b) / steps
+    sites = shape[0] * shape[1] * shape[2]
+    peak, peak_kind = measured_peak()
+    achieved = BYTES_PER_SITE["f32"] * sites / (ms * 1e-3) / 1e9
+    return {"workload": "D3Q19 64x64x256 slab, A-rich band of width 128, E6 stencil, G_AA c_s^2 = -0.2, FP32",
+            "MLUPS": sites / (ms * 1e-3) / 1e6, "kernel_ms": ms, "launch": sim.step_config,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "bytes_per_site": BYTES_PER_SITE["f32"], "peak_source": peak_kind}}
 
 
 def alt_throughput(B, storage, args, dev, stream):
@@ -548,6 +584,62 @@ def precision_study(args, dev):
         del sim
         torch.cuda.empty_cache()
     out["large_droplet"] = big
+    print(json.dumps(out), flush=True)
+
+
+def large_droplet_study(args, dev):
+    """The large droplet of the workload configurations at a formed droplet: side --study-size (default 256,
+    the half-size fallback of 512^3), R = 3 side / 16, asymmetric couplings (G_AA c_s^2 = -0.2), psi =
+    exp(-1/n), --study-large-steps time steps in every storage.  The pressure jump of Eq. bulkp is
+    recorded every 2^11 steps (section 4's check interval) with its relative change; dP, R_s, sigma_s,
+    densities and velocity of FP32, FP16 and BF16 storage are compared with the FP64-storage run."""
+    import torch
+
+    import sc_synth
+    from paper_2112_02574_gb300 import binding as B
+
+    n = args.study_size
+    shape = (n, n, n)
+    R = n * 3.0 / 16.0
+    T = args.study_large_steps
+    nA0, nB0 = sc_synth.droplet(shape, (n // 2,) * 3, R, n_in=0.95, n_out=0.05, amplitude=1e-3)
+    kw = dict(lattice=B.SC_D3Q19, psi_self=B.SC_PSI_EXP, G=G_CROSS, G_self=(-0.6, 0.0))
+    out = {"study": "large droplet at a formed droplet", "shape": list(shape), "R": R, "steps": T,
+           "couplings": {"G": G_CROSS, "G_self": [-0.6, 0.0]}}
+
+    def run(storage):
+        t0 = time.perf_counter()
+        sim = B.Simulation(B.make_params(shape, storage=storage, **kw), nA0, nB0, device=dev)
+        jump = lambda: float((sim.bulk_pressure((n // 2,) * 3) - sim.bulk_pressure((n - 1,) * 3)).item())
+        hist, t, prev = [], 0, None
+        while t < T:
+            w = min(2048, T - t)
+            sim.step(w)
+            t += w
+            dp = jump()
+            hist.append([t, dp, abs(dp - prev) / abs(prev) if prev else None])
+            prev = dp
+        _, o = B.surface_of_tension(sim, (n // 2,) * 3, 0.5)
+        nA, nB, u = sim.moments()
+        sim.sync()
+        o = o.cpu().numpy()
+        res = {"dP": float(o[0]), "R_s": float(o[2]), "sigma_s": float(o[3]), "dP_history": hist,
+               "seconds": time.perf_counter() - t0}
+        return res, (nA, nB, u), sim
+
+    ref, (rA, rB, ru), sim = run(B.SC_STORE_F64)
+    del sim
+    torch.cuda.empty_cache()
+    out["f64"] = ref
+    for name, code in (("f32", B.SC_STORE_F32), ("f16", B.SC_STORE_F16), ("bf16", B.SC_STORE_BF16)):
+        res, (nA, nB, u), sim = run(code)
+        res["errors_vs_f64"] = {
+            **{k + "_rel": abs(res[k] - ref[k]) / abs(ref[k]) for k in ("dP", "R_s", "sigma_s")},
+            "n_max_rel": max(float((nA - rA).abs().max() / rA.abs().max()), float((nB - rB).abs().max() / rB.abs().max())),
+            "u_max_abs": float((u - ru).abs().max()), "u_max": float(ru.abs().max())}
+        out[name] = res
+        del sim, nA, nB, u
+        torch.cuda.empty_cache()
     print(json.dumps(out), flush=True)
 
 
@@ -679,16 +771,18 @@ def paper_tolman_study(args, dev):
         args.study_storage]
     T = args.study_steps
     ntot = args.study_density
+    sides = tuple(int(v) for v in args.study_sides.split(",")) if args.study_sides else PAPER_SIDES
+    dgabs = tuple(float(v) for v in args.study_dgab.split(",")) if args.study_dgab else PAPER_DGAB
     out = {"study": "Tolman length on the couplings of Eq. self_p (dG_c = 0.4, G c_s^2 = 0.5, psi = exp(-1/n))",
-           "steps": T, "storage": args.study_storage, "total_density": ntot, "sides": list(PAPER_SIDES), "sets": {}}
+           "steps": T, "storage": args.study_storage, "total_density": ntot, "sides": list(sides), "sets": {}}
     members, flats = [], {}
-    for d in PAPER_DGAB:
+    for d in dgabs:
         kw = dict(lattice=B.SC_D3Q19, psi_self=B.SC_PSI_EXP, storage=code, **paper_couplings(d))
         slab = lambda shape: sc_synth.slab(shape, shape[0] / 2, n_rich=0.95 * ntot, n_poor=0.05 * ntot,
                                            amplitude=1e-3)
         fl = tolman.flat_densities((16, 16, 128), slab, kw, T, device=dev)
         flats[d] = fl
-        for L in PAPER_SIDES:
+        for L in sides:
             for sign in (1, -1):
                 inside = (fl["A_in"], fl["B_in"]) if sign > 0 else (fl["A_out"], fl["B_out"])
                 outside = (fl["A_out"], fl["B_out"]) if sign > 0 else (fl["A_in"], fl["B_in"])
@@ -703,11 +797,14 @@ def paper_tolman_study(args, dev):
                          "droplets retire from the batch; at most --study-steps steps"
     import torch
 
-    for d in PAPER_DGAB:
+    for d in dgabs:
         ds = [x for x in drops if x["tag"] == d]
         s0 = torch.tensor([flats[d]["sigma0"]], dtype=torch.float64, device=dev)
+        free = tolman.fit(ds, None, device=dev)
         out["sets"][f"{d:+.2f}"] = {"flat": flats[d], "fit_fixed_sigma0": tolman.fit(ds, s0, device=dev),
-                                    "fit_free_sigma0": tolman.fit(ds, None, device=dev),
+                                    "fit_free_sigma0": free,
+                                    # section 4, Fig. 3a: the droplets' R_s -> infinity limit against the slab
+                                    "sigma0_limit_vs_slab": (free["sigma0"] - flats[d]["sigma0"]) / flats[d]["sigma0"],
                                     "converged": sum(1 for x in ds if x["converged"]),
                                     "steps_range": [min(x["steps"] for x in ds), max(x["steps"] for x in ds)],
                                     "max_com_offset": max(x["com_offset"] for x in ds),
@@ -736,7 +833,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched radius sweep block")
     ap.add_argument("--inner", type=int, default=INNER, help="time steps per benchmark step (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--study", choices=["precision", "paper", "configs"],
+    ap.add_argument("--study", choices=["precision", "paper", "configs", "large"],
                     help="run only a study (minutes) and print its JSON line: precision = every result in each "
                          "storage against the FP64 path; paper = Tolman length on the couplings of Eq. self_p; "
                          "configs = GPU and oracle rates of every workload configuration")
@@ -747,6 +844,9 @@ def main():
     ap.add_argument("--study-steps", type=int, default=16384, help="time steps of the Tolman sweep and slab")
     ap.add_argument("--study-size", type=int, default=512, help="side of the large droplet of the study")
     ap.add_argument("--study-size-steps", type=int, default=4096, help="time steps of the large droplet")
+    ap.add_argument("--study-sides", default="", help="paper study: comma-separated cube sides (default: 25..65)")
+    ap.add_argument("--study-dgab", default="", help="paper study: comma-separated dG_AB values")
+    ap.add_argument("--study-large-steps", type=int, default=16384, help="large study: time steps per storage")
     args = ap.parse_args()
     INNER = args.inner
     rank = int(os.environ.get("RANK", "0"))
@@ -765,8 +865,8 @@ def main():
         return
     if args.study:
         if rank == 0:
-            {"precision": precision_study, "paper": paper_tolman_study, "configs": configs_study}[args.study](
-                args, "cuda")
+            {"precision": precision_study, "paper": paper_tolman_study, "configs": configs_study,
+             "large": large_droplet_study}[args.study](args, "cuda")
         return
     if world > 1:
         import torch

@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "../../include/sc.h"
 
 namespace scgb {
@@ -183,15 +185,17 @@ struct Codec2<double, double> {
     *reinterpret_cast<double2 *>(p) = v;
   }
 };
+// F16 pairs are read and written in scaled units (see scaled_units below): the step
+// arithmetic itself carries the power-of-two scale, so no multiply happens here.
 template <>
 struct Codec2<__half, float> {
   template <bool SMEM>
-  __device__ __forceinline__ static float2 load(const __half *p, float2 inv_scale) {
+  __device__ __forceinline__ static float2 load(const __half *p, float2) {
     const __half2 h = SMEM ? *reinterpret_cast<const __half2 *>(p) : __ldg(reinterpret_cast<const __half2 *>(p));
-    return pmul(__half22float2(h), inv_scale);
+    return __half22float2(h);
   }
-  __device__ __forceinline__ static void store(__half *p, float2 v, float2 scale) {
-    *reinterpret_cast<__half2 *>(p) = __float22half2_rn(pmul(v, scale));
+  __device__ __forceinline__ static void store(__half *p, float2 v, float2) {
+    *reinterpret_cast<__half2 *>(p) = __float22half2_rn(v);
   }
 };
 template <>
@@ -206,6 +210,19 @@ struct Codec2<__nv_bfloat16, float> {
     *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(v);
   }
 };
+
+// Units of the step arithmetic.  F16 storage keeps its values multiplied by a
+// power-of-two scale 2^k(J) per component; its step computes the population
+// pairs in those scaled units directly (the weights w_i enter as w_i 2^k, sums
+// and momenta are scaled back once), which saves a multiply per population read
+// and per population written.  A power of two commutes with every rounding (no
+// value is near the FP32 range limits), so the results are bit for bit those of
+// the same arithmetic on unscaled values.  Every other storage computes on the
+// values themselves.
+template <class ST>
+__host__ __device__ constexpr bool scaled_units() {
+  return std::is_same<ST, __half>::value;
+}
 
 // ---------------------------------------------------------------- arguments
 template <class CT>

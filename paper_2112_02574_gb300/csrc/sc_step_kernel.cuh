@@ -27,13 +27,32 @@
 
 namespace scgb {
 
+// Weight w_i of direction i as a component pair, in the step's units (scaled_units).
+template <int LAT, class ST, class CT>
+__device__ __forceinline__ P2<CT> wpair(int i, P2<CT> scale) {
+  if constexpr (scaled_units<ST>()) return pmul(pbc(CT(Lattice<LAT>::w(i))), scale);
+  return pbc(CT(Lattice<LAT>::w(i)));
+}
+// -w_i likewise.
+template <int LAT, class ST, class CT>
+__device__ __forceinline__ P2<CT> wpair_neg(int i, P2<CT> scale) {
+  if constexpr (scaled_units<ST>()) return pmul(pbc(CT(-Lattice<LAT>::w(i))), scale);
+  return pbc(CT(-Lattice<LAT>::w(i)));
+}
+// A sum of pairs in the step's units, as a natural value.
+template <class ST, class CT>
+__device__ __forceinline__ P2<CT> unscale(P2<CT> v, P2<CT> inv_scale) {
+  if constexpr (scaled_units<ST>()) return pmul(v, inv_scale);
+  return v;
+}
+
 // Pull the Q population pairs arriving at site (gx, gy, gz) and return their
-// sum (the density deviations); values go to v[] when V is true.  Values are
-// deviations from w_i nbar; with a local reference the source site's density
-// deviation nsrc[s] = n(s) - nbar enters as w_i nsrc[s].
+// sum (the density deviations, natural units); values go to v[] (step units) when
+// V is true.  Values are deviations from w_i nbar; with a local reference the source
+// site's density deviation nsrc[s] = n(s) - nbar enters as w_i nsrc[s].
 template <int LAT, class ST, class CT, bool V>
 __device__ __forceinline__ P2<CT> pull_site(const ST *__restrict__ src, int gx, int gy, int gz, int nx, int ny,
-                                            int nz, int64_t N, P2<CT> inv_scale, P2<CT> *v,
+                                            int nz, int64_t N, P2<CT> scale, P2<CT> inv_scale, P2<CT> *v,
                                             const float2 *__restrict__ nsrc = nullptr) {
   using L = Lattice<LAT>;
   // source coordinate for velocity component c is g - c
@@ -48,12 +67,12 @@ __device__ __forceinline__ P2<CT> pull_site(const ST *__restrict__ src, int gx, 
     P2<CT> g = Codec2<ST, CT>::template load<false>(src + ((int64_t)i * N + site) * 2, inv_scale);
     if constexpr (local_ref<ST>()) {
       const float2 ns = __ldg(nsrc + site);
-      g = pfma(pbc(CT(L::w(i))), pset(CT(ns.x), CT(ns.y)), g);
+      g = pfma(wpair<LAT, ST, CT>(i, scale), pset(CT(ns.x), CT(ns.y)), g);
     }
     if (V) v[i] = g;
     sum = padd(sum, g);
   }
-  return sum;
+  return unscale<ST, CT>(sum, inv_scale);
 }
 
 // psi(n) - psi(nbar) per component; for psi = exp(-1/n): psibar * expm1((n - nbar) / (n nbar)).
@@ -115,9 +134,9 @@ __device__ __forceinline__ void force_pair(const StepArgs<CT> &a, const P2<CT> *
 }
 
 // Half momenta h_J = j_J + F_J / 2 with j_J = sum_i g_i xi_i from opposite-pair differences.
-template <int LAT, class CT>
+template <int LAT, class ST, class CT>
 __device__ __forceinline__ void half_momentum(const P2<CT> (&g)[Lattice<LAT>::Q], const P2<CT> (&F)[3],
-                                              P2<CT> (&h)[3]) {
+                                              P2<CT> inv_scale, P2<CT> (&h)[3]) {
   using L = Lattice<LAT>;
   constexpr int Q = L::Q;
   P2<CT> d[Q];
@@ -132,7 +151,7 @@ __device__ __forceinline__ void half_momentum(const P2<CT> (&g)[Lattice<LAT>::Q]
       if (cm > 0) acc = padd(acc, d[i]);
       if (cm < 0) acc = psub(acc, d[i]);
     }
-    h[m] = pfma(pbc(CT(0.5)), F[m], acc);
+    h[m] = pfma(pbc(CT(0.5)), F[m], unscale<ST, CT>(acc, inv_scale));
   }
 }
 
@@ -151,7 +170,7 @@ __device__ __forceinline__ void common_velocity(const P2<CT> (&h)[3], P2<CT> n, 
 //   a0 = omega dn - 1.5 omega n u.u - 3 gamma u.F, a1 = 3 omega n,
 //   a2 = 4.5 omega n, a3 = 9 gamma, a4 = 3 gamma
 // (Eq. feq with c_s^2 = 1/3 written as a deviation from w_i nbar, and Eq. Guo).
-template <int LAT, class CT>
+template <int LAT, class ST, class CT>
 __device__ __forceinline__ void collide_pair(const StepArgs<CT> &a, const P2<CT> (&g)[Lattice<LAT>::Q], P2<CT> n,
                                              P2<CT> dn, const CT (&u)[3], const P2<CT> (&F)[3],
                                              P2<CT> (&out)[Lattice<LAT>::Q]) {
@@ -165,11 +184,11 @@ __device__ __forceinline__ void collide_pair(const StepArgs<CT> &a, const P2<CT>
   const P2<CT> a1 = pmul(pmul(pbc(CT(3)), om), n), a2 = pmul(pmul(pbc(CT(4.5)), om), n);
   const P2<CT> a3 = pmul(pbc(CT(9)), ga), a4 = pmul(pbc(CT(3)), ga);
   const P2<CT> keep = psub(pbc(CT(1)), om);
-  out[0] = pfma(keep, g[0], pmul(pbc(CT(L::w(0))), a0));
+  out[0] = pfma(keep, g[0], pmul(wpair<LAT, ST, CT>(0, a.scale), a0));
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
     const int c[3] = {L::c(i, 0), L::c(i, 1), L::c(i, 2)};
-    const P2<CT> w = pbc(CT(L::w(i)));
+    const P2<CT> w = wpair<LAT, ST, CT>(i, a.scale);
     CT cu = CT(0);
     P2<CT> cF = pbc(CT(0));
 #pragma unroll
@@ -202,7 +221,7 @@ __device__ __forceinline__ void store_pairs(const StepArgs<CT> &a, ST *__restric
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     P2<CT> v = out[i];
-    if constexpr (local_ref<ST>()) v = pfma(pbc(CT(-Lattice<LAT>::w(i))), dn, v);
+    if constexpr (local_ref<ST>()) v = pfma(wpair_neg<LAT, ST, CT>(i, a.scale), dn, v);
     Codec2<ST, CT>::store(dst + ((int64_t)i * a.N + site) * 2, v, a.scale);
   }
   if constexpr (local_ref<ST>()) a.ndst[site] = make_float2(float(dn.x), float(dn.y));
@@ -223,9 +242,9 @@ __device__ __forceinline__ void collide_site(const StepArgs<CT> &a, const P2<CT>
   P2<CT> F[3], h[3], out[Q];
   CT u[3];
   force_pair<LAT, STEN, CT, TY>(a, s_dn, s_psi, sl, own, n, psi, F);
-  half_momentum<LAT, CT>(g, F, h);
+  half_momentum<LAT, ST, CT>(g, F, a.inv_scale, h);
   common_velocity<CT>(h, n, u);
-  collide_pair<LAT, CT>(a, g, n, dn, u, F, out);
+  collide_pair<LAT, ST, CT>(a, g, n, dn, u, F, out);
   if (valid) {
     check_density<CT>(a, n);
     store_pairs<LAT, ST, CT, Q>(a, dst, site, out, n, dn);
@@ -312,7 +331,7 @@ __device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by
     // ---- density / psi deviations of this plane: own site
     {
       const P2<CT> dn =
-          pull_site<LAT, ST, CT, KEEP>(src, gx, gy, gz, nx, ny, nz, N, a.inv_scale, nxt, a.nsrc);
+          pull_site<LAT, ST, CT, KEEP>(src, gx, gy, gz, nx, ny, nz, N, a.scale, a.inv_scale, nxt, a.nsrc);
       s_dn[slot * PLANE + own] = dn;
       if (a.self_on) s_psi[slot * PLANE + own] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp);
     }
@@ -330,7 +349,7 @@ __device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by
       }
       const int hx = ((x0 + px) % nx + nx) % nx, hy = ((y0 + py) % ny + ny) % ny;
       const P2<CT> dn =
-          pull_site<LAT, ST, CT, false>(src, hx, hy, gz, nx, ny, nz, N, a.inv_scale, nullptr, a.nsrc);
+          pull_site<LAT, ST, CT, false>(src, hx, hy, gz, nx, ny, nz, N, a.scale, a.inv_scale, nullptr, a.nsrc);
       const int idx = (py + H) * SX + (px + H);
       s_dn[slot * PLANE + idx] = dn;
       if (a.self_on) s_psi[slot * PLANE + idx] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp);
@@ -348,7 +367,7 @@ __device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by
       if (HZ == 1) {
         collide_site<LAT, STEN, ST, CT, TY>(a, cur, s_dn, s_psi, sl, own, valid_xy, dst, site);
       } else {
-        if (!KEEP) pull_site<LAT, ST, CT, true>(src, gx, gy, gzc, nx, ny, nz, N, a.inv_scale, nxt, a.nsrc);
+        if (!KEEP) pull_site<LAT, ST, CT, true>(src, gx, gy, gzc, nx, ny, nz, N, a.scale, a.inv_scale, nxt, a.nsrc);
         collide_site<LAT, STEN, ST, CT, TY>(a, nxt, s_dn, s_psi, sl, own, valid_xy, dst, site);
       }
     }

@@ -89,12 +89,13 @@ constexpr size_t staged_smem_bytes(bool self_on = true) {
 }
 
 // Sum of the Q staged population pairs arriving at tile position (px, py), in
-// direction order (identical to pull_site's order); values go to v[] when V is true.
+// direction order (identical to pull_site's order), in natural units; values go to
+// v[] (step units, see scaled_units) when V is true.
 // With a local reference, nring + nsl[1 - c^z] is the plane of density deviations
 // n - nbar of the source plane z - c^z.
 template <class ST, class CT, int TY, bool V>
 __device__ __forceinline__ P2<CT> staged_sum(const ST *stage, const float2 *nring, const int (&nsl)[3], int px,
-                                             int py, P2<CT> inv_scale, P2<CT> *v) {
+                                             int py, P2<CT> scale, P2<CT> inv_scale, P2<CT> *v) {
   using G = StagedGeom<ST, TY>;
   using L = Lattice<kD3Q19>;
   const ST *base = stage + ((py + 1) * G::WX + px + G::OFF) * 2;
@@ -105,12 +106,12 @@ __device__ __forceinline__ P2<CT> staged_sum(const ST *stage, const float2 *nrin
     if constexpr (G::LOCAL) {
       // density deviation of the source site (x - c_i, y - c_i^y, plane z - c_i^z)
       const float2 ns = nring[nsl[1 - L::c(i, 2)] + (py - L::c(i, 1) + 2) * G::WXN + px + G::OFFN - L::c(i, 0)];
-      g = pfma(pbc(CT(L::w(i))), pset(CT(ns.x), CT(ns.y)), g);
+      g = pfma(wpair<kD3Q19, ST, CT>(i, scale), pset(CT(ns.x), CT(ns.y)), g);
     }
     if (V) v[i] = g;
     sum = padd(sum, g);
   }
-  return sum;
+  return unscale<ST, CT>(sum, inv_scale);
 }
 
 // One block's column (bx, by), planes z0 .. zend - 1, of the lattice described by a,
@@ -283,7 +284,7 @@ __device__ __forceinline__ void staged_block(const StepArgs<CT> &a, int bx, int 
     if (k + NS < np) rows_for(wrapz(zk(k + NS)));
     const int slot = k & (G::NPL - 1);
     {
-      const P2<CT> dn = staged_sum<ST, CT, TY, true>(stage, nring, nsl, tx, ty, a.inv_scale, mine);
+      const P2<CT> dn = staged_sum<ST, CT, TY, true>(stage, nring, nsl, tx, ty, a.scale, a.inv_scale, mine);
       s_dn[slot * G::PLANE + own] = dn;
       if (a.self_on) s_psi[slot * G::PLANE + own] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp);
     }
@@ -291,7 +292,7 @@ __device__ __forceinline__ void staged_block(const StepArgs<CT> &a, int bx, int 
     for (int m = 0; m < NTASK; ++m) {
       if (task_on[m]) {
         const P2<CT> dn =
-            staged_sum<ST, CT, TY, false>(stage, nring, nsl, task_px[m], task_py[m], a.inv_scale, nullptr);
+            staged_sum<ST, CT, TY, false>(stage, nring, nsl, task_px[m], task_py[m], a.scale, a.inv_scale, nullptr);
         s_dn[slot * G::PLANE + task_idx[m]] = dn;
         if (a.self_on) s_psi[slot * G::PLANE + task_idx[m]] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp);
       }

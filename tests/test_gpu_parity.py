@@ -72,6 +72,8 @@ CASES = [
     ((35, 10, 18), 1, 1, 1, (-0.4, 0.2)),
     ((70, 45, 1), 0, 0, 0, (0.0, 0.0)),
     ((33, 13, 1), 0, 0, 1, (-0.3, 0.0)),
+    # whole 32-site x tiles and whole y tiles of every tile_y (the bench workload's tiling)
+    ((64, 16, 12), 1, 0, 1, (-0.4, 0.0)),
 ]
 
 
