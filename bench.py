@@ -801,10 +801,18 @@ def paper_tolman_study(args, dev):
         ds = [x for x in drops if x["tag"] == d]
         s0 = torch.tensor([flats[d]["sigma0"]], dtype=torch.float64, device=dev)
         free = tolman.fit(ds, None, device=dev)
+        # section 4, Fig. 3a: the droplets' R_s -> infinity limit (Eq. sigma_c with sigma_0 free) against the
+        # slab, over all sizes and over the larger sizes only (the expansion in 1/R_s holds better there)
+        limits = {}
+        for lmin in sorted({min(sides), 51, 97}):
+            sub = [x for x in ds if x["L"] >= lmin]
+            f = tolman.fit(sub, None, device=dev)
+            limits[f"L>={lmin}"] = {"sigma0": f["sigma0"], "delta": f["delta"], "used": f["used"],
+                                    "rel_to_slab": (f["sigma0"] - flats[d]["sigma0"]) / flats[d]["sigma0"]}
         out["sets"][f"{d:+.2f}"] = {"flat": flats[d], "fit_fixed_sigma0": tolman.fit(ds, s0, device=dev),
                                     "fit_free_sigma0": free,
-                                    # section 4, Fig. 3a: the droplets' R_s -> infinity limit against the slab
                                     "sigma0_limit_vs_slab": (free["sigma0"] - flats[d]["sigma0"]) / flats[d]["sigma0"],
+                                    "droplet_limit_by_size": limits,
                                     "converged": sum(1 for x in ds if x["converged"]),
                                     "steps_range": [min(x["steps"] for x in ds), max(x["steps"] for x in ds)],
                                     "max_com_offset": max(x["com_offset"] for x in ds),

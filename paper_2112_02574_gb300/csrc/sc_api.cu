@@ -82,6 +82,8 @@ int default_tile_y(const sc_params *p) {
 // blocks, with and without a self coupling (128^3 .. 512^3, same-box comparisons);
 // F64 keeps two stages (three of its blocks do not fit in registers).
 bool has_self(const sc_params *p) { return p->G_self[0] != 0.0 || p->G_self[1] != 0.0; }
+// tau_A = tau_B = 1: the step kernels' instantiation that carries momentum sums instead of populations.
+bool tau_one(const sc_params *p) { return p->tau[0] == 1.0 && p->tau[1] == 1.0; }
 int effective_stages(const sc_params *p, int tile_y) {
   if (p->stages) return p->stages;
   if (tile_y == 4) return p->storage == SC_STORE_F64 ? 2 : 1;
@@ -352,6 +354,7 @@ StepArgs<CT> step_args(sc_ctx *c) {
   a.inv_scale = pair<CT>(c->inv_scale[0][0], c->inv_scale[1][0]);
   a.gcross = CT(-c->p.G * cs2);
   a.self_on = (c->p.G_self[0] != 0.0 || c->p.G_self[1] != 0.0) ? 1 : 0;
+  a.tau_one = tau_one(&c->p) ? 1 : 0;
   a.psi_exp = c->p.psi_self == SC_PSI_EXP ? 1 : 0;
   a.err = status_word(c);
   a.nsrc = c->L.ref_bytes ? reinterpret_cast<const float2 *>(c->ws + c->L.off_ref[c->cur]) : nullptr;
@@ -386,23 +389,23 @@ sc_status plan_z_split(sc_ctx *c) {
   // L2 instead of a staged window.
   const int target_chunk = !c->staged ? kGenericTargetChunk : (is_16bit(c->p.storage) ? 36 : 18);
   int dev = 0, sms = 0, occ = 0;
-  const bool self_on = has_self(&c->p);
+  const bool self_on = has_self(&c->p), t1 = tau_one(&c->p);
   const int lat = c->p.lattice == SC_D3Q19 ? kD3Q19 : kD2Q9, sten = c->p.stencil == SC_FORCE_E6 ? kE6 : kE4;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess && c->staged) {
     switch (c->p.storage) {
-      case SC_STORE_F32: e = staged_occupancy_f32(c->tile_y, c->stages, c->blocks_per_sm, self_on, &occ); break;
-      case SC_STORE_F16: e = staged_occupancy_f16(c->tile_y, c->stages, c->blocks_per_sm, self_on, &occ); break;
-      case SC_STORE_BF16: e = staged_occupancy_bf16(c->tile_y, c->stages, c->blocks_per_sm, self_on, &occ); break;
-      default: e = staged_occupancy_f64(c->tile_y, c->stages, c->blocks_per_sm, self_on, &occ); break;
+      case SC_STORE_F32: e = staged_occupancy_f32(c->tile_y, c->stages, c->blocks_per_sm, self_on, t1, &occ); break;
+      case SC_STORE_F16: e = staged_occupancy_f16(c->tile_y, c->stages, c->blocks_per_sm, self_on, t1, &occ); break;
+      case SC_STORE_BF16: e = staged_occupancy_bf16(c->tile_y, c->stages, c->blocks_per_sm, self_on, t1, &occ); break;
+      default: e = staged_occupancy_f64(c->tile_y, c->stages, c->blocks_per_sm, self_on, t1, &occ); break;
     }
   } else if (e == cudaSuccess) {
     switch (c->p.storage) {
-      case SC_STORE_F32: e = generic_occupancy_f32(lat, sten, c->tile_y, &occ); break;
-      case SC_STORE_F16: e = generic_occupancy_f16(lat, sten, c->tile_y, &occ); break;
-      case SC_STORE_BF16: e = generic_occupancy_bf16(lat, sten, c->tile_y, &occ); break;
-      default: e = generic_occupancy_f64(lat, sten, c->tile_y, &occ); break;
+      case SC_STORE_F32: e = generic_occupancy_f32(lat, sten, c->tile_y, t1, &occ); break;
+      case SC_STORE_F16: e = generic_occupancy_f16(lat, sten, c->tile_y, t1, &occ); break;
+      case SC_STORE_BF16: e = generic_occupancy_bf16(lat, sten, c->tile_y, t1, &occ); break;
+      default: e = generic_occupancy_f64(lat, sten, c->tile_y, t1, &occ); break;
     }
   }
   if (e != cudaSuccess) return fail(SC_ECUDA, "occupancy of the step kernel: %s", cudaGetErrorString(e));
@@ -1190,22 +1193,24 @@ sc_status sc_batch_create(int32_t n, const sc_params *params, const double *cons
   const int lat = params[0].lattice == SC_D3Q19 ? kD3Q19 : kD2Q9;
   const int sten = params[0].stencil == SC_FORCE_E6 ? kE6 : kE4;
   b->staged = staged ? 1 : 0;
+  bool all_t1 = true;  // every member has tau_A = tau_B = 1: the momentum-carry instantiation
+  for (int k = 0; k < n; ++k) all_t1 = all_t1 && tau_one(&params[k]);
   if (staged) {
     const int ns = b->ctx[0]->stages, mb = b->ctx[0]->blocks_per_sm;
     bool any_self = false;
     for (int k = 0; k < n; ++k) any_self = any_self || has_self(&params[k]);
     switch (storage) {
-      case SC_STORE_F32: b->kernel = batched_staged_kernel_f32(b->tile_y, ns, mb, any_self, &b->smem); break;
-      case SC_STORE_F16: b->kernel = batched_staged_kernel_f16(b->tile_y, ns, mb, any_self, &b->smem); break;
-      case SC_STORE_BF16: b->kernel = batched_staged_kernel_bf16(b->tile_y, ns, mb, any_self, &b->smem); break;
-      default: b->kernel = batched_staged_kernel_f64(b->tile_y, ns, mb, any_self, &b->smem); break;
+      case SC_STORE_F32: b->kernel = batched_staged_kernel_f32(b->tile_y, ns, mb, any_self, all_t1, &b->smem); break;
+      case SC_STORE_F16: b->kernel = batched_staged_kernel_f16(b->tile_y, ns, mb, any_self, all_t1, &b->smem); break;
+      case SC_STORE_BF16: b->kernel = batched_staged_kernel_bf16(b->tile_y, ns, mb, any_self, all_t1, &b->smem); break;
+      default: b->kernel = batched_staged_kernel_f64(b->tile_y, ns, mb, any_self, all_t1, &b->smem); break;
     }
   } else {
     switch (storage) {
-      case SC_STORE_F32: b->kernel = batched_kernel_f32(lat, sten, b->tile_y, &b->smem); break;
-      case SC_STORE_F16: b->kernel = batched_kernel_f16(lat, sten, b->tile_y, &b->smem); break;
-      case SC_STORE_BF16: b->kernel = batched_kernel_bf16(lat, sten, b->tile_y, &b->smem); break;
-      default: b->kernel = batched_kernel_f64(lat, sten, b->tile_y, &b->smem); break;
+      case SC_STORE_F32: b->kernel = batched_kernel_f32(lat, sten, b->tile_y, all_t1, &b->smem); break;
+      case SC_STORE_F16: b->kernel = batched_kernel_f16(lat, sten, b->tile_y, all_t1, &b->smem); break;
+      case SC_STORE_BF16: b->kernel = batched_kernel_bf16(lat, sten, b->tile_y, all_t1, &b->smem); break;
+      default: b->kernel = batched_kernel_f64(lat, sten, b->tile_y, all_t1, &b->smem); break;
     }
   }
   if (!b->kernel) {

@@ -238,6 +238,7 @@ struct StepArgs {
   P2<CT> gself;      // -G_JJ c_s^2
   P2<CT> psibar;     // psi(nbar_J)
   int self_on;       // any G_JJ != 0
+  int tau_one;       // tau_A = tau_B = 1: the relaxation keeps nothing of f (see carry_size)
   int psi_exp;       // psi = exp(-1/n) (else psi = n)
   P2<CT> scale;      // storage scale 2^k(J) (F16; unused for the other storages)
   P2<CT> inv_scale;  // 2^-k(J)

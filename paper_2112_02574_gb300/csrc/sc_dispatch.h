@@ -28,31 +28,36 @@ cudaError_t launch_step_f64(const StepLaunch &l, const StepArgs<double> &a);
 // The batched step kernel for one (lattice, stencil, tile_y) combination, as a
 // function pointer for graph kernel nodes (nullptr if unsupported); *smem
 // receives its dynamic shared-memory bytes.  Parameters: (const StepArgs *args,
-// const int4 *items, int swap), block (32, tile_y), one block per item.
-const void *batched_kernel_f32(int lattice, int stencil, int tile_y, size_t *smem);
-const void *batched_kernel_f16(int lattice, int stencil, int tile_y, size_t *smem);
-const void *batched_kernel_bf16(int lattice, int stencil, int tile_y, size_t *smem);
-const void *batched_kernel_f64(int lattice, int stencil, int tile_y, size_t *smem);
+// const int4 *items, int swap), block (32, tile_y), one block per item.  t1: every
+// member has tau_A = tau_B = 1 (the instantiation that carries momentum sums only).
+const void *batched_kernel_f32(int lattice, int stencil, int tile_y, bool t1, size_t *smem);
+const void *batched_kernel_f16(int lattice, int stencil, int tile_y, bool t1, size_t *smem);
+const void *batched_kernel_bf16(int lattice, int stencil, int tile_y, bool t1, size_t *smem);
+const void *batched_kernel_f64(int lattice, int stencil, int tile_y, bool t1, size_t *smem);
 
 // Resident blocks per SM of the staged step kernel for (tile_y, stages, blocks_per_sm),
 // with or without the psi ring of a self coupling.
-cudaError_t staged_occupancy_f32(int tile_y, int stages, int blocks_per_sm, bool self_on, int *blocks);
-cudaError_t staged_occupancy_f16(int tile_y, int stages, int blocks_per_sm, bool self_on, int *blocks);
-cudaError_t staged_occupancy_bf16(int tile_y, int stages, int blocks_per_sm, bool self_on, int *blocks);
-cudaError_t staged_occupancy_f64(int tile_y, int stages, int blocks_per_sm, bool self_on, int *blocks);
+cudaError_t staged_occupancy_f32(int tile_y, int stages, int blocks_per_sm, bool self_on, bool t1, int *blocks);
+cudaError_t staged_occupancy_f16(int tile_y, int stages, int blocks_per_sm, bool self_on, bool t1, int *blocks);
+cudaError_t staged_occupancy_bf16(int tile_y, int stages, int blocks_per_sm, bool self_on, bool t1, int *blocks);
+cudaError_t staged_occupancy_f64(int tile_y, int stages, int blocks_per_sm, bool self_on, bool t1, int *blocks);
 
 // Resident blocks per SM of the generic step kernel for (lattice, stencil, tile_y).
-cudaError_t generic_occupancy_f32(int lattice, int stencil, int tile_y, int *blocks);
-cudaError_t generic_occupancy_f16(int lattice, int stencil, int tile_y, int *blocks);
-cudaError_t generic_occupancy_bf16(int lattice, int stencil, int tile_y, int *blocks);
-cudaError_t generic_occupancy_f64(int lattice, int stencil, int tile_y, int *blocks);
+cudaError_t generic_occupancy_f32(int lattice, int stencil, int tile_y, bool t1, int *blocks);
+cudaError_t generic_occupancy_f16(int lattice, int stencil, int tile_y, bool t1, int *blocks);
+cudaError_t generic_occupancy_bf16(int lattice, int stencil, int tile_y, bool t1, int *blocks);
+cudaError_t generic_occupancy_f64(int lattice, int stencil, int tile_y, bool t1, int *blocks);
 
 // The batched staged step kernel (D3Q19, E4) for (tile_y, stages, blocks_per_sm),
 // same parameters and block shape as above; nullptr if not instantiated.  self_on:
 // some member has a self coupling (the psi ring is then part of *smem).
-const void *batched_staged_kernel_f32(int tile_y, int stages, int blocks_per_sm, bool self_on, size_t *smem);
-const void *batched_staged_kernel_f16(int tile_y, int stages, int blocks_per_sm, bool self_on, size_t *smem);
-const void *batched_staged_kernel_bf16(int tile_y, int stages, int blocks_per_sm, bool self_on, size_t *smem);
-const void *batched_staged_kernel_f64(int tile_y, int stages, int blocks_per_sm, bool self_on, size_t *smem);
+const void *batched_staged_kernel_f32(int tile_y, int stages, int blocks_per_sm, bool self_on, bool t1,
+                                         size_t *smem);
+const void *batched_staged_kernel_f16(int tile_y, int stages, int blocks_per_sm, bool self_on, bool t1,
+                                         size_t *smem);
+const void *batched_staged_kernel_bf16(int tile_y, int stages, int blocks_per_sm, bool self_on, bool t1,
+                                         size_t *smem);
+const void *batched_staged_kernel_f64(int tile_y, int stages, int blocks_per_sm, bool self_on, bool t1,
+                                         size_t *smem);
 
 }  // namespace scgb

@@ -3,16 +3,17 @@
 cudaError_t scgb::launch_step_bf16(const StepLaunch &l, const StepArgs<float> &a) {
   return launch_any<__nv_bfloat16, float>(l, a);
 }
-const void *scgb::batched_kernel_bf16(int lattice, int stencil, int tile_y, size_t *smem) {
-  return batched_any<__nv_bfloat16, float>(lattice, stencil, tile_y, smem);
+const void *scgb::batched_kernel_bf16(int lattice, int stencil, int tile_y, bool t1, size_t *smem) {
+  return batched_any<__nv_bfloat16, float>(lattice, stencil, tile_y, t1, smem);
 }
-const void *scgb::batched_staged_kernel_bf16(int tile_y, int stages, int blocks_per_sm, bool self_on,
-                                             size_t *smem) {
-  return batched_staged_any<__nv_bfloat16, float>(tile_y, stages, blocks_per_sm, self_on, smem);
+const void *scgb::batched_staged_kernel_bf16(int tile_y, int stages, int blocks_per_sm, bool self_on, bool t1,
+                                               size_t *smem) {
+  return batched_staged_any<__nv_bfloat16, float>(tile_y, stages, blocks_per_sm, self_on, t1, smem);
 }
-cudaError_t scgb::staged_occupancy_bf16(int tile_y, int stages, int blocks_per_sm, bool self_on, int *blocks) {
-  return staged_occupancy<__nv_bfloat16, float>(tile_y, stages, blocks_per_sm, self_on, blocks);
+cudaError_t scgb::staged_occupancy_bf16(int tile_y, int stages, int blocks_per_sm, bool self_on, bool t1,
+                                       int *blocks) {
+  return staged_occupancy<__nv_bfloat16, float>(tile_y, stages, blocks_per_sm, self_on, t1, blocks);
 }
-cudaError_t scgb::generic_occupancy_bf16(int lattice, int stencil, int tile_y, int *blocks) {
-  return generic_occupancy<__nv_bfloat16, float>(lattice, stencil, tile_y, blocks);
+cudaError_t scgb::generic_occupancy_bf16(int lattice, int stencil, int tile_y, bool t1, int *blocks) {
+  return generic_occupancy<__nv_bfloat16, float>(lattice, stencil, tile_y, t1, blocks);
 }

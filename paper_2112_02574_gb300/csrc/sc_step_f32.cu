@@ -1,16 +1,17 @@
 // Step-kernel instantiations: FP32 deviation storage, FP32 collision.
 #include "sc_step_inst.cuh"
 cudaError_t scgb::launch_step_f32(const StepLaunch &l, const StepArgs<float> &a) { return launch_any<float, float>(l, a); }
-const void *scgb::batched_kernel_f32(int lattice, int stencil, int tile_y, size_t *smem) {
-  return batched_any<float, float>(lattice, stencil, tile_y, smem);
+const void *scgb::batched_kernel_f32(int lattice, int stencil, int tile_y, bool t1, size_t *smem) {
+  return batched_any<float, float>(lattice, stencil, tile_y, t1, smem);
 }
-const void *scgb::batched_staged_kernel_f32(int tile_y, int stages, int blocks_per_sm, bool self_on,
-                                             size_t *smem) {
-  return batched_staged_any<float, float>(tile_y, stages, blocks_per_sm, self_on, smem);
+const void *scgb::batched_staged_kernel_f32(int tile_y, int stages, int blocks_per_sm, bool self_on, bool t1,
+                                               size_t *smem) {
+  return batched_staged_any<float, float>(tile_y, stages, blocks_per_sm, self_on, t1, smem);
 }
-cudaError_t scgb::staged_occupancy_f32(int tile_y, int stages, int blocks_per_sm, bool self_on, int *blocks) {
-  return staged_occupancy<float, float>(tile_y, stages, blocks_per_sm, self_on, blocks);
+cudaError_t scgb::staged_occupancy_f32(int tile_y, int stages, int blocks_per_sm, bool self_on, bool t1,
+                                       int *blocks) {
+  return staged_occupancy<float, float>(tile_y, stages, blocks_per_sm, self_on, t1, blocks);
 }
-cudaError_t scgb::generic_occupancy_f32(int lattice, int stencil, int tile_y, int *blocks) {
-  return generic_occupancy<float, float>(lattice, stencil, tile_y, blocks);
+cudaError_t scgb::generic_occupancy_f32(int lattice, int stencil, int tile_y, bool t1, int *blocks) {
+  return generic_occupancy<float, float>(lattice, stencil, tile_y, t1, blocks);
 }

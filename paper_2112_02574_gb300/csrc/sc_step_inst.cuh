@@ -27,10 +27,11 @@ inline bool attr_once(const void *k, size_t smem) {
   return true;
 }
 
+// T1 selects the tau_A = tau_B = 1 instantiation (StepArgs::tau_one).
 template <int LAT, int STEN, class ST, class CT, int TY>
 cudaError_t launch_one(const StepLaunch &l, const StepArgs<CT> &a) {
   constexpr size_t smem = step_smem_bytes<LAT, STEN, CT, TY>();
-  auto *k = sc_step_kernel<LAT, STEN, ST, CT, TY>;
+  auto *k = a.tau_one ? sc_step_kernel<LAT, STEN, ST, CT, TY, true> : sc_step_kernel<LAT, STEN, ST, CT, TY, false>;
   if (!attr_once(reinterpret_cast<const void *>(k), smem)) return cudaGetLastError();
   const dim3 grid = a.zbal_k > 0 ? dim3(a.zbal_k * a.zbal_cols + a.zbal_rem) : l.grid;
   k<<<grid, dim3(32, TY), smem, l.stream>>>(a);
@@ -38,9 +39,9 @@ cudaError_t launch_one(const StepLaunch &l, const StepArgs<CT> &a) {
 }
 
 template <int LAT, int STEN, class ST, class CT, int TY>
-cudaError_t generic_occupancy_one(int *blocks) {
+cudaError_t generic_occupancy_one(bool t1, int *blocks) {
   constexpr size_t smem = step_smem_bytes<LAT, STEN, CT, TY>();
-  auto *k = sc_step_kernel<LAT, STEN, ST, CT, TY>;
+  auto *k = t1 ? sc_step_kernel<LAT, STEN, ST, CT, TY, true> : sc_step_kernel<LAT, STEN, ST, CT, TY, false>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, 32 * TY, smem);
@@ -48,14 +49,14 @@ cudaError_t generic_occupancy_one(int *blocks) {
 
 // Resident blocks per SM of the generic kernel for (lattice, stencil, tile_y).
 template <class ST, class CT>
-cudaError_t generic_occupancy(int lat, int sten, int ty, int *blocks) {
+cudaError_t generic_occupancy(int lat, int sten, int ty, bool t1, int *blocks) {
   auto by_ty = [&](auto lat_c, auto sten_c) -> cudaError_t {
     constexpr int LAT = decltype(lat_c)::value, STEN = decltype(sten_c)::value;
     switch (ty) {
-      case 1: return generic_occupancy_one<LAT, STEN, ST, CT, 1>(blocks);
-      case 2: return generic_occupancy_one<LAT, STEN, ST, CT, 2>(blocks);
-      case 4: return generic_occupancy_one<LAT, STEN, ST, CT, 4>(blocks);
-      case 8: return generic_occupancy_one<LAT, STEN, ST, CT, 8>(blocks);
+      case 1: return generic_occupancy_one<LAT, STEN, ST, CT, 1>(t1, blocks);
+      case 2: return generic_occupancy_one<LAT, STEN, ST, CT, 2>(t1, blocks);
+      case 4: return generic_occupancy_one<LAT, STEN, ST, CT, 4>(t1, blocks);
+      case 8: return generic_occupancy_one<LAT, STEN, ST, CT, 8>(t1, blocks);
       default: return cudaErrorInvalidValue;
     }
   };
@@ -70,7 +71,7 @@ template <class ST, class CT, int TY, int NS, int MINB>
 cudaError_t launch_staged_one(const StepLaunch &l, const StepArgs<CT> &a) {
   constexpr size_t smem_max = staged_smem_bytes<ST, CT, TY, NS>();
   const size_t smem = staged_smem_bytes<ST, CT, TY, NS>(a.self_on != 0);
-  auto *k = sc_step_staged<ST, CT, TY, NS, MINB>;
+  auto *k = a.tau_one ? sc_step_staged<ST, CT, TY, NS, MINB, true> : sc_step_staged<ST, CT, TY, NS, MINB, false>;
   if (!attr_once(reinterpret_cast<const void *>(k), smem_max)) return cudaGetLastError();
   const dim3 grid = a.zbal_k > 0 ? dim3(a.zbal_k * a.zbal_cols + a.zbal_rem)
                                  : dim3((a.nx + 31) / 32, (a.ny + TY - 1) / TY, (a.nz + a.tile_z - 1) / a.tile_z);
@@ -79,8 +80,8 @@ cudaError_t launch_staged_one(const StepLaunch &l, const StepArgs<CT> &a) {
 }
 
 template <class ST, class CT, int TY, int NS, int MINB>
-cudaError_t staged_occupancy_one(bool self_on, int *blocks) {
-  auto *k = sc_step_staged<ST, CT, TY, NS, MINB>;
+cudaError_t staged_occupancy_one(bool self_on, bool t1, int *blocks) {
+  auto *k = t1 ? sc_step_staged<ST, CT, TY, NS, MINB, true> : sc_step_staged<ST, CT, TY, NS, MINB, false>;
   cudaError_t e =
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(staged_smem_bytes<ST, CT, TY, NS>()));
   if (e != cudaSuccess) return e;
@@ -126,10 +127,10 @@ R with_staged_cfg(int ty, int ns, int mb, R fallback, Fn &&fn) {
 
 // Resident blocks per SM of the staged kernel for (tile_y, stages, blocks_per_sm).
 template <class ST, class CT>
-cudaError_t staged_occupancy(int ty, int ns, int mb, bool self_on, int *blocks) {
+cudaError_t staged_occupancy(int ty, int ns, int mb, bool self_on, bool t1, int *blocks) {
   return with_staged_cfg<ST>(ty, ns, mb, cudaErrorInvalidValue, [&](auto cfg) {
     using C = decltype(cfg);
-    return staged_occupancy_one<ST, CT, C::TY, C::NS, C::MINB>(self_on, blocks);
+    return staged_occupancy_one<ST, CT, C::TY, C::NS, C::MINB>(self_on, t1, blocks);
   });
 }
 
@@ -164,36 +165,36 @@ cudaError_t launch_any(const StepLaunch &l, const StepArgs<CT> &a) {
 }
 
 template <int LAT, int STEN, class ST, class CT, int TY>
-const void *batched_one(size_t *smem) {
+const void *batched_one(bool t1, size_t *smem) {
   constexpr size_t bytes = step_smem_bytes<LAT, STEN, CT, TY>();
-  auto *k = sc_step_batched<LAT, STEN, ST, CT, TY>;
+  auto *k = t1 ? sc_step_batched<LAT, STEN, ST, CT, TY, true> : sc_step_batched<LAT, STEN, ST, CT, TY, false>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)) != cudaSuccess) return nullptr;
   *smem = bytes;
   return reinterpret_cast<const void *>(k);
 }
 
 template <int LAT, int STEN, class ST, class CT>
-const void *batched_ty(int ty, size_t *smem) {
+const void *batched_ty(int ty, bool t1, size_t *smem) {
   switch (ty) {
-    case 1: return batched_one<LAT, STEN, ST, CT, 1>(smem);
-    case 2: return batched_one<LAT, STEN, ST, CT, 2>(smem);
-    case 4: return batched_one<LAT, STEN, ST, CT, 4>(smem);
-    case 8: return batched_one<LAT, STEN, ST, CT, 8>(smem);
+    case 1: return batched_one<LAT, STEN, ST, CT, 1>(t1, smem);
+    case 2: return batched_one<LAT, STEN, ST, CT, 2>(t1, smem);
+    case 4: return batched_one<LAT, STEN, ST, CT, 4>(t1, smem);
+    case 8: return batched_one<LAT, STEN, ST, CT, 8>(t1, smem);
     default: return nullptr;
   }
 }
 
 template <class ST, class CT>
-const void *batched_any(int lat, int sten, int ty, size_t *smem) {
-  if (lat == kD3Q19 && sten == kE4) return batched_ty<kD3Q19, kE4, ST, CT>(ty, smem);
-  if (lat == kD3Q19 && sten == kE6) return batched_ty<kD3Q19, kE6, ST, CT>(ty, smem);
-  if (lat == kD2Q9 && sten == kE4) return batched_ty<kD2Q9, kE4, ST, CT>(ty, smem);
+const void *batched_any(int lat, int sten, int ty, bool t1, size_t *smem) {
+  if (lat == kD3Q19 && sten == kE4) return batched_ty<kD3Q19, kE4, ST, CT>(ty, t1, smem);
+  if (lat == kD3Q19 && sten == kE6) return batched_ty<kD3Q19, kE6, ST, CT>(ty, t1, smem);
+  if (lat == kD2Q9 && sten == kE4) return batched_ty<kD2Q9, kE4, ST, CT>(ty, t1, smem);
   return nullptr;
 }
 
 template <class ST, class CT, int TY, int NS, int MINB>
-const void *batched_staged_one(bool self_on, size_t *smem) {
-  auto *k = sc_step_staged_batched<ST, CT, TY, NS, MINB>;
+const void *batched_staged_one(bool self_on, bool t1, size_t *smem) {
+  auto *k = t1 ? sc_step_staged_batched<ST, CT, TY, NS, MINB, true> : sc_step_staged_batched<ST, CT, TY, NS, MINB, false>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            int(staged_smem_bytes<ST, CT, TY, NS>())) != cudaSuccess)
     return nullptr;
@@ -203,10 +204,10 @@ const void *batched_staged_one(bool self_on, size_t *smem) {
 
 // Same configurations as launch_staged.
 template <class ST, class CT>
-const void *batched_staged_any(int ty, int ns, int mb, bool self_on, size_t *smem) {
+const void *batched_staged_any(int ty, int ns, int mb, bool self_on, bool t1, size_t *smem) {
   return with_staged_cfg<ST>(ty, ns, mb, static_cast<const void *>(nullptr), [&](auto cfg) {
     using C = decltype(cfg);
-    return batched_staged_one<ST, CT, C::TY, C::NS, C::MINB>(self_on, smem);
+    return batched_staged_one<ST, CT, C::TY, C::NS, C::MINB>(self_on, t1, smem);
   });
 }
 

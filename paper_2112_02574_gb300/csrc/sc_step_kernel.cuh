@@ -133,10 +133,9 @@ __device__ __forceinline__ void force_pair(const StepArgs<CT> &a, const P2<CT> *
   for (int m = 0; m < 3; ++m) F[m] = pfma(cp, T[m], pmul(cn, pswap(S[m])));
 }
 
-// Half momenta h_J = j_J + F_J / 2 with j_J = sum_i g_i xi_i from opposite-pair differences.
-template <int LAT, class ST, class CT>
-__device__ __forceinline__ void half_momentum(const P2<CT> (&g)[Lattice<LAT>::Q], const P2<CT> (&F)[3],
-                                              P2<CT> inv_scale, P2<CT> (&h)[3]) {
+// Momentum sums j_J = sum_i g_i xi_i (step units) from opposite-pair differences.
+template <int LAT, class CT>
+__device__ __forceinline__ void momentum_sums(const P2<CT> *g, P2<CT> (&j)[3]) {
   using L = Lattice<LAT>;
   constexpr int Q = L::Q;
   P2<CT> d[Q];
@@ -151,7 +150,35 @@ __device__ __forceinline__ void half_momentum(const P2<CT> (&g)[Lattice<LAT>::Q]
       if (cm > 0) acc = padd(acc, d[i]);
       if (cm < 0) acc = psub(acc, d[i]);
     }
-    h[m] = pfma(pbc(CT(0.5)), F[m], unscale<ST, CT>(acc, inv_scale));
+    j[m] = acc;
+  }
+}
+
+// Half momenta h_J = j_J + F_J / 2.
+template <class ST, class CT>
+__device__ __forceinline__ void half_momentum(const P2<CT> (&j)[3], const P2<CT> (&F)[3], P2<CT> inv_scale,
+                                              P2<CT> (&h)[3]) {
+#pragma unroll
+  for (int m = 0; m < 3; ++m) h[m] = pfma(pbc(CT(0.5)), F[m], unscale<ST, CT>(j[m], inv_scale));
+}
+
+// What a site's collision needs of its own arriving populations.  In general the
+// population pairs themselves (CARRY = Q pairs).  With tau_A = tau_B = 1 (T1) the
+// relaxation keeps nothing of them, (1 - 1/tau) f_i = 0, and only their momentum
+// sums enter (CARRY = 3 pairs): the kernels then keep those across the planes between
+// a site's sum and its collision, and the stored results are the same bits.
+template <int LAT, bool T1>
+__host__ __device__ constexpr int carry_size() {
+  return T1 ? 3 : Lattice<LAT>::Q;
+}
+// The carry of a site from its arriving pairs g (step units).
+template <int LAT, class CT, bool T1>
+__device__ __forceinline__ void make_carry(const P2<CT> (&g)[Lattice<LAT>::Q], P2<CT> (&c)[carry_size<LAT, T1>()]) {
+  if constexpr (T1) {
+    momentum_sums<LAT, CT>(g, c);
+  } else {
+#pragma unroll
+    for (int i = 0; i < Lattice<LAT>::Q; ++i) c[i] = g[i];
   }
 }
 
@@ -170,9 +197,10 @@ __device__ __forceinline__ void common_velocity(const P2<CT> (&h)[3], P2<CT> n, 
 //   a0 = omega dn - 1.5 omega n u.u - 3 gamma u.F, a1 = 3 omega n,
 //   a2 = 4.5 omega n, a3 = 9 gamma, a4 = 3 gamma
 // (Eq. feq with c_s^2 = 1/3 written as a deviation from w_i nbar, and Eq. Guo).
-template <int LAT, class ST, class CT>
-__device__ __forceinline__ void collide_pair(const StepArgs<CT> &a, const P2<CT> (&g)[Lattice<LAT>::Q], P2<CT> n,
-                                             P2<CT> dn, const CT (&u)[3], const P2<CT> (&F)[3],
+// T1 (tau_A = tau_B = 1): keep = 1 - omega = 0 and g is not read (fma(0, g, x) = x).
+template <int LAT, class ST, class CT, bool T1>
+__device__ __forceinline__ void collide_pair(const StepArgs<CT> &a, const P2<CT> *g, P2<CT> n, P2<CT> dn,
+                                             const CT (&u)[3], const P2<CT> (&F)[3],
                                              P2<CT> (&out)[Lattice<LAT>::Q]) {
   using L = Lattice<LAT>;
   constexpr int Q = L::Q;
@@ -184,7 +212,7 @@ __device__ __forceinline__ void collide_pair(const StepArgs<CT> &a, const P2<CT>
   const P2<CT> a1 = pmul(pmul(pbc(CT(3)), om), n), a2 = pmul(pmul(pbc(CT(4.5)), om), n);
   const P2<CT> a3 = pmul(pbc(CT(9)), ga), a4 = pmul(pbc(CT(3)), ga);
   const P2<CT> keep = psub(pbc(CT(1)), om);
-  out[0] = pfma(keep, g[0], pmul(wpair<LAT, ST, CT>(0, a.scale), a0));
+  out[0] = T1 ? pmul(wpair<LAT, ST, CT>(0, a.scale), a0) : pfma(keep, g[0], pmul(wpair<LAT, ST, CT>(0, a.scale), a0));
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
     const int c[3] = {L::c(i, 0), L::c(i, 1), L::c(i, 2)};
@@ -199,8 +227,13 @@ __device__ __forceinline__ void collide_pair(const StepArgs<CT> &a, const P2<CT>
     const P2<CT> cu2 = pbc(cu);
     const P2<CT> E = pfma(cu2, pfma(pmul(w, a2), cu2, pmul(pmul(w, a3), cF)), pmul(w, a0));
     const P2<CT> O = pfma(pmul(w, a1), cu2, pmul(pmul(w, a4), cF));
-    out[i] = pfma(keep, g[i], padd(E, O));
-    out[i + 1] = pfma(keep, g[i + 1], psub(E, O));
+    if constexpr (T1) {
+      out[i] = padd(E, O);
+      out[i + 1] = psub(E, O);
+    } else {
+      out[i] = pfma(keep, g[i], padd(E, O));
+      out[i + 1] = pfma(keep, g[i + 1], psub(E, O));
+    }
   }
 }
 
@@ -227,9 +260,9 @@ __device__ __forceinline__ void store_pairs(const StepArgs<CT> &a, ST *__restric
   if constexpr (local_ref<ST>()) a.ndst[site] = make_float2(float(dn.x), float(dn.y));
 }
 
-// Collision of one site from its arriving population pairs g[i] and the ring.
-template <int LAT, int STEN, class ST, class CT, int TY>
-__device__ __forceinline__ void collide_site(const StepArgs<CT> &a, const P2<CT> (&g)[Lattice<LAT>::Q],
+// Collision of one site from the carry of its arriving population pairs and the ring.
+template <int LAT, int STEN, class ST, class CT, int TY, bool T1>
+__device__ __forceinline__ void collide_site(const StepArgs<CT> &a, const P2<CT> (&carry)[carry_size<LAT, T1>()],
                                              const P2<CT> *s_dn, const P2<CT> *s_psi, const int *sl, int own,
                                              bool valid, ST *__restrict__ dst, int64_t site) {
   constexpr int Q = Lattice<LAT>::Q;
@@ -239,12 +272,18 @@ __device__ __forceinline__ void collide_site(const StepArgs<CT> &a, const P2<CT>
   const P2<CT> dn = s_dn[sl[HZ] * PLANE + own];
   const P2<CT> n = padd(a.nbar, dn);
   const P2<CT> psi = a.self_on ? padd(a.psibar, s_psi[sl[HZ] * PLANE + own]) : pbc(CT(0));
-  P2<CT> F[3], h[3], out[Q];
+  P2<CT> F[3], j[3], h[3], out[Q];
   CT u[3];
   force_pair<LAT, STEN, CT, TY>(a, s_dn, s_psi, sl, own, n, psi, F);
-  half_momentum<LAT, ST, CT>(g, F, a.inv_scale, h);
+  if constexpr (T1) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) j[m] = carry[m];
+  } else {
+    momentum_sums<LAT, CT>(carry, j);
+  }
+  half_momentum<ST, CT>(j, F, a.inv_scale, h);
   common_velocity<CT>(h, n, u);
-  collide_pair<LAT, ST, CT>(a, g, n, dn, u, F, out);
+  collide_pair<LAT, ST, CT, T1>(a, carry, n, dn, u, F, out);
   if (valid) {
     check_density<CT>(a, n);
     store_pairs<LAT, ST, CT, Q>(a, dst, site, out, n, dn);
@@ -293,7 +332,7 @@ __device__ __forceinline__ void block_work(const StepArgs<CT> &a, int &bx, int &
 
 // One block's work: the column (bx, by), planes z0 .. zend - 1, of the lattice described by a,
 // marched upward or (down) downward.
-template <int LAT, int STEN, class ST, class CT, int TY>
+template <int LAT, int STEN, class ST, class CT, int TY, bool T1>
 __device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by, int z0, int zend, bool down,
                                            unsigned char *smem_raw) {
   using L = Lattice<LAT>;
@@ -306,7 +345,11 @@ __device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by
   constexpr int PLANE = SX * SY;
   constexpr int NHALO = PLANE - 32 * TY;
   constexpr int NT = 32 * TY;
-  constexpr bool KEEP = (HZ <= 1);  // own populations stay in registers until collided
+  // a site's carry (its own populations, or with T1 their momentum sums) stays in registers
+  // from its sum to its collision HZ planes later; the general E6 form pulls the site again
+  constexpr bool KEEP = T1 || (HZ <= 1);
+  constexpr int CQ = carry_size<LAT, T1>();
+  constexpr int NC = KEEP ? HZ + 1 : 1;  // carries in flight: planes m - HZ .. m
 
   P2<CT> *s_dn = reinterpret_cast<P2<CT> *>(smem_raw);  // [NPL][PLANE]
   P2<CT> *s_psi = s_dn + NPL * PLANE;                   // [NPL][PLANE]
@@ -322,7 +365,7 @@ __device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by
   const int gx = (x0 + tx) % nx, gy = (y0 + ty) % ny;
   const int own = (ty + H) * SX + (tx + H);
 
-  P2<CT> cur[Q], nxt[Q];
+  P2<CT> car[NC][CQ];
   int slot = 0;
   const int np = zend - z0 + 2 * HZ;  // planes z0 - HZ .. zend - 1 + HZ, in march order m
   for (int m = 0; m < np; ++m) {
@@ -330,10 +373,18 @@ __device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by
     const int gz = ((p % nz) + nz) % nz;
     // ---- density / psi deviations of this plane: own site
     {
+      P2<CT> g[Q];
       const P2<CT> dn =
-          pull_site<LAT, ST, CT, KEEP>(src, gx, gy, gz, nx, ny, nz, N, a.scale, a.inv_scale, nxt, a.nsrc);
+          pull_site<LAT, ST, CT, KEEP>(src, gx, gy, gz, nx, ny, nz, N, a.scale, a.inv_scale, g, a.nsrc);
       s_dn[slot * PLANE + own] = dn;
       if (a.self_on) s_psi[slot * PLANE + own] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp);
+      if constexpr (KEEP) {
+#pragma unroll
+        for (int q = 0; q + 1 < NC; ++q)
+#pragma unroll
+          for (int i = 0; i < CQ; ++i) car[q][i] = car[q + 1][i];
+        make_carry<LAT, CT, T1>(g, car[NC - 1]);
+      }
     }
     // ---- halo sites (full rows first, for coalescing, then the side columns)
     for (int h = tid; h < NHALO; h += NT) {
@@ -364,34 +415,32 @@ __device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by
       for (int d = 0; d <= 2 * HZ; ++d) sl[d] = (down ? slot - d + NPL : slot - 2 * HZ + d + 2 * NPL) % NPL;
       const int gzc = ((c % nz) + nz) % nz;
       const int64_t site = (int64_t)gx + (int64_t)nx * (gy + (int64_t)ny * gzc);
-      if (HZ == 1) {
-        collide_site<LAT, STEN, ST, CT, TY>(a, cur, s_dn, s_psi, sl, own, valid_xy, dst, site);
+      if constexpr (KEEP) {
+        collide_site<LAT, STEN, ST, CT, TY, T1>(a, car[0], s_dn, s_psi, sl, own, valid_xy, dst, site);
       } else {
-        if (!KEEP) pull_site<LAT, ST, CT, true>(src, gx, gy, gzc, nx, ny, nz, N, a.scale, a.inv_scale, nxt, a.nsrc);
-        collide_site<LAT, STEN, ST, CT, TY>(a, nxt, s_dn, s_psi, sl, own, valid_xy, dst, site);
+        P2<CT> g[Q];
+        pull_site<LAT, ST, CT, true>(src, gx, gy, gzc, nx, ny, nz, N, a.scale, a.inv_scale, g, a.nsrc);
+        collide_site<LAT, STEN, ST, CT, TY, T1>(a, g, s_dn, s_psi, sl, own, valid_xy, dst, site);
       }
-    }
-    if (HZ == 1) {
-#pragma unroll
-      for (int i = 0; i < Q; ++i) cur[i] = nxt[i];
     }
     slot = (slot + 1 == NPL) ? 0 : slot + 1;
   }
 }
 
-template <int LAT, int STEN, class ST, class CT, int TY>
+// T1: the tau_A = tau_B = 1 form (see carry_size).
+template <int LAT, int STEN, class ST, class CT, int TY, bool T1>
 __global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 16 / TY)) sc_step_kernel(const StepArgs<CT> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   int bx, by, z0, zend;
   bool down;
   block_work(a, bx, by, z0, zend, down);
-  step_block<LAT, STEN, ST, CT, TY>(a, bx, by, z0, zend, down, smem_raw);
+  step_block<LAT, STEN, ST, CT, TY, T1>(a, bx, by, z0, zend, down, smem_raw);
 }
 
 // Batched form: one launch steps several lattices.  Block b works on item
 // items[b] = (lattice, bx, by, bz); lattice l's arguments are args[l] (read
 // from global memory), with source and destination swapped when swap != 0.
-template <int LAT, int STEN, class ST, class CT, int TY>
+template <int LAT, int STEN, class ST, class CT, int TY, bool T1>
 __global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 16 / TY))
     sc_step_batched(const StepArgs<CT> *__restrict__ args, const int4 *__restrict__ items, int swap) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -406,7 +455,7 @@ __global__ void __launch_bounds__(32 * TY, (TY >= 16 ? 1 : 16 / TY))
     a.ndst = const_cast<float2 *>(u);
   }
   const int z0 = it.w * a.tile_z;
-  step_block<LAT, STEN, ST, CT, TY>(a, it.y, it.z, z0, min(z0 + a.tile_z, a.nz), false, smem_raw);
+  step_block<LAT, STEN, ST, CT, TY, T1>(a, it.y, it.z, z0, min(z0 + a.tile_z, a.nz), false, smem_raw);
 }
 
 }  // namespace scgb

@@ -119,13 +119,14 @@ __device__ __forceinline__ P2<CT> staged_sum(const ST *stage, const float2 *nrin
 // NS: pipeline stages (2: the copy of plane k + 2 overlaps sum k and collide k - 1;
 // 1: the copy of plane k + 1 overlaps collide k - 1 only, for half the stage memory).
 // Window x coordinates wrap once: every chunk start lies in [-nx, 2 nx) for nx >= 32.
-template <class ST, class CT, int TY, int NS>
+template <class ST, class CT, int TY, int NS, bool T1>
 __device__ __forceinline__ void staged_block(const StepArgs<CT> &a, int bx, int by, int z0, int zend, bool down,
                                              unsigned char *smem_raw) {
   static_assert(NS == 1 || NS == 2, "one or two pipeline stages");
   using G = StagedGeom<ST, TY>;
   using L = Lattice<kD3Q19>;
   constexpr int Q = G::Q;
+  constexpr int CQ = carry_size<kD3Q19, T1>();
   constexpr int NT = 32 * TY;
   constexpr int NTASK = (G::NHALO + NT - 1) / NT;  // halo sums per thread and plane
   ST *stage0 = reinterpret_cast<ST *>(smem_raw);                                // [NS][STAGE_ELEMS]
@@ -268,9 +269,9 @@ __device__ __forceinline__ void staged_block(const StepArgs<CT> &a, int bx, int 
     cp_async_commit();
   }
 
-  // one plane of the march: sum plane k (own population pairs into `mine`),
+  // one plane of the march: sum plane k (the own site's carry into `mine`),
   // then collide plane k - 1 from `prev`
-  auto body = [&](int k, P2<CT> (&prev)[Q], P2<CT> (&mine)[Q]) {
+  auto body = [&](int k, P2<CT> (&prev)[CQ], P2<CT> (&mine)[CQ]) {
     const int s = NS == 2 ? (k & 1) : 0;
     const ST *stage = stage0 + s * G::STAGE_ELEMS;
     // density planes of z - 1, z, z + 1 (z = zk(k)): density positions k .. k + 2 (reversed down)
@@ -284,7 +285,9 @@ __device__ __forceinline__ void staged_block(const StepArgs<CT> &a, int bx, int 
     if (k + NS < np) rows_for(wrapz(zk(k + NS)));
     const int slot = k & (G::NPL - 1);
     {
-      const P2<CT> dn = staged_sum<ST, CT, TY, true>(stage, nring, nsl, tx, ty, a.scale, a.inv_scale, mine);
+      P2<CT> g[Q];
+      const P2<CT> dn = staged_sum<ST, CT, TY, true>(stage, nring, nsl, tx, ty, a.scale, a.inv_scale, g);
+      make_carry<kD3Q19, CT, T1>(g, mine);
       s_dn[slot * G::PLANE + own] = dn;
       if (a.self_on) s_psi[slot * G::PLANE + own] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp);
     }
@@ -308,10 +311,10 @@ __device__ __forceinline__ void staged_block(const StepArgs<CT> &a, int bx, int 
       const int sl[3] = {down ? slot : s_lo, (slot + 3) & 3, down ? s_lo : slot};
       const int c = zk(k - 1);
       const int64_t site = (int64_t)gx + (int64_t)nx * (gy + (int64_t)ny * c);
-      collide_site<kD3Q19, kE4, ST, CT, TY>(a, prev, s_dn, s_psi, sl, own, valid_xy, dst, site);
+      collide_site<kD3Q19, kE4, ST, CT, TY, T1>(a, prev, s_dn, s_psi, sl, own, valid_xy, dst, site);
     }
   };
-  P2<CT> A[Q], B[Q];
+  P2<CT> A[CQ], B[CQ];
   int k = 0;
   for (; k + 1 < np; k += 2) {
     body(k, B, A);
@@ -320,20 +323,21 @@ __device__ __forceinline__ void staged_block(const StepArgs<CT> &a, int bx, int 
   if (k < np) body(k, B, A);
 }
 
-// MINB: resident blocks per SM the register allocation must allow.
-template <class ST, class CT, int TY, int NS, int MINB>
+// MINB: resident blocks per SM the register allocation must allow; T1: the
+// tau_A = tau_B = 1 form (see carry_size).
+template <class ST, class CT, int TY, int NS, int MINB, bool T1>
 __global__ void __launch_bounds__(32 * TY, MINB) sc_step_staged(const StepArgs<CT> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   int bx, by, z0, zend;
   bool down;
   block_work(a, bx, by, z0, zend, down);
-  staged_block<ST, CT, TY, NS>(a, bx, by, z0, zend, down, smem_raw);
+  staged_block<ST, CT, TY, NS, T1>(a, bx, by, z0, zend, down, smem_raw);
 }
 
 // Batched form (see sc_step_batched): block b works on items[b] = (lattice, bx,
 // by, bz) with the arguments args[lattice], source and destination swapped when
 // swap != 0.
-template <class ST, class CT, int TY, int NS, int MINB>
+template <class ST, class CT, int TY, int NS, int MINB, bool T1>
 __global__ void __launch_bounds__(32 * TY, MINB)
     sc_step_staged_batched(const StepArgs<CT> *__restrict__ args, const int4 *__restrict__ items, int swap) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -354,7 +358,7 @@ __global__ void __launch_bounds__(32 * TY, MINB)
   }
   __syncthreads();
   const int z0 = it.w * s_a.tile_z;
-  staged_block<ST, CT, TY, NS>(s_a, it.y, it.z, z0, min(z0 + s_a.tile_z, s_a.nz), false, smem_raw);
+  staged_block<ST, CT, TY, NS, T1>(s_a, it.y, it.z, z0, min(z0 + s_a.tile_z, s_a.nz), false, smem_raw);
 }
 
 }  // namespace scgb
