@@ -418,7 +418,7 @@ def sweep_droplets():
     return out
 
 
-BATCH_CANDIDATES = [(8, 64, 1, 2), (4, 32, 1, 3), (4, 64, 1, 3), (4, 128, 1, 3), (4, 64, 2, 2)]
+BATCH_CANDIDATES = [(8, 64, 1, 3), (8, 64, 1, 2), (4, 32, 1, 3), (4, 64, 1, 3), (4, 128, 1, 3), (4, 64, 2, 2)]
 
 
 def batch_block(B, dev, stream, plain_mlups, steps=128):

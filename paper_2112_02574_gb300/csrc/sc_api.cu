@@ -68,7 +68,16 @@ bool staged_eligible(const sc_params *p, int tile_y) {
 
 // Kernel choice and tiles (measured sweeps at 128^3, 256^3 and 512^3 set the defaults).
 bool is_16bit(int storage) { return storage == SC_STORE_F16 || storage == SC_STORE_BF16; }
-int staged_default_tile_y(const sc_params *p) { return is_16bit(p->storage) ? 8 : 4; }
+// tau_A = tau_B = 1: the step kernels' instantiation that carries momentum sums instead of populations.
+bool tau_one(const sc_params *p) { return p->tau[0] == 1.0 && p->tau[1] == 1.0; }
+// Tile 32 x 8 for 16-bit storage, and for FP32 with tau = 1, whose momentum carry leaves room for three
+// 8-warp blocks per SM (80 registers, no spills; same box at 128^3: FP32 126.3 -> 120.0 us against tile
+// 32 x 4 with four blocks, FP16 101.5 -> 98.0 us against two blocks per SM); FP64 and FP32 with tau != 1
+// keep tile 32 x 4 (their populations carried across the plane delay need the registers).
+int staged_default_tile_y(const sc_params *p) {
+  if (is_16bit(p->storage)) return 8;
+  return (p->storage == SC_STORE_F32 && tau_one(p)) ? 8 : 4;
+}
 bool use_staged(const sc_params *p) {
   if (p->variant == 1) return false;
   return staged_eligible(p, p->tile_y ? p->tile_y : staged_default_tile_y(p));
@@ -82,8 +91,7 @@ int default_tile_y(const sc_params *p) {
 // blocks, with and without a self coupling (128^3 .. 512^3, same-box comparisons);
 // F64 keeps two stages (three of its blocks do not fit in registers).
 bool has_self(const sc_params *p) { return p->G_self[0] != 0.0 || p->G_self[1] != 0.0; }
-// tau_A = tau_B = 1: the step kernels' instantiation that carries momentum sums instead of populations.
-bool tau_one(const sc_params *p) { return p->tau[0] == 1.0 && p->tau[1] == 1.0; }
+
 int effective_stages(const sc_params *p, int tile_y) {
   if (p->stages) return p->stages;
   if (tile_y == 4) return p->storage == SC_STORE_F64 ? 2 : 1;
@@ -92,7 +100,8 @@ int effective_stages(const sc_params *p, int tile_y) {
 int effective_blocks_per_sm(const sc_params *p, int tile_y) {
   if (p->blocks_per_sm) return p->blocks_per_sm;
   if (tile_y == 4) return p->storage == SC_STORE_F64 ? 2 : 3;
-  return tile_y == 16 ? 1 : 2;
+  if (tile_y == 8) return (tau_one(p) && effective_stages(p, tile_y) == 1) ? 3 : 2;
+  return 1;
 }
 int default_tile_z(const sc_params *p) {
   if (p->lattice == SC_D2Q9) return 1;
@@ -116,7 +125,7 @@ sc_status validate(const sc_params *p) {
   if (p->tile_y == 16 && !use_staged(p)) return fail(SC_EINVAL, "tile_y 16 needs the staged kernel");
   if (use_staged(p)) {
     const int ty = default_tile_y(p);
-    const int lo = ty == 4 ? 2 : 1, hi = ty == 4 ? 3 : (ty == 8 ? 2 : 1);
+    const int lo = ty == 4 ? 2 : 1, hi = ty == 4 ? 3 : (ty == 8 ? (effective_stages(p, ty) == 1 ? 3 : 2) : 1);
     if (p->blocks_per_sm && (p->blocks_per_sm < lo || p->blocks_per_sm > hi))
       return fail(SC_EINVAL, "blocks_per_sm must be 0 or %d .. %d for the staged kernel with tile_y %d", lo, hi, ty);
     if (ty == 16 && effective_stages(p, ty) == 2 && !is_16bit(p->storage))

@@ -114,6 +114,7 @@ R with_staged_cfg(int ty, int ns, int mb, R fallback, Fn &&fn) {
       if (ns == 2 && mb == 2) return fn(StagedCfg<8, 2, 2>{});
       if (ns == 1 && mb <= 1) return fn(StagedCfg<8, 1, 1>{});
       if (ns == 1 && mb == 2) return fn(StagedCfg<8, 1, 2>{});
+      if (ns == 1 && mb == 3) return fn(StagedCfg<8, 1, 3>{});
     }
     if (ty == 16 && mb <= 1) {
       if (ns == 1) return fn(StagedCfg<16, 1, 1>{});

@@ -15,7 +15,7 @@ from . import binding as B
 # candidate is the library default, so the tuner never returns a slower configuration than it.
 DEFAULT = [(0, 0, 0, 0, 0)]
 STAGED = [(2, 4, 0, 1, 3), (2, 4, 0, 2, 2), (2, 4, 16, 1, 3), (2, 4, 32, 1, 3), (2, 4, 16, 2, 3),
-          (2, 8, 0, 1, 2), (2, 8, 0, 1, 1), (2, 8, 16, 2, 1), (2, 8, 32, 1, 2)]
+          (2, 8, 0, 1, 3), (2, 8, 0, 1, 2), (2, 8, 0, 1, 1), (2, 8, 16, 2, 1), (2, 8, 32, 1, 2)]
 GENERIC = [(1, 8, 0, 0, 0), (1, 4, 0, 0, 0), (1, 8, 16, 0, 0), (1, 8, 32, 0, 0), (1, 4, 32, 0, 0)]
 CHUNK_SITES = {B.SC_STORE_F64: 1, B.SC_STORE_F32: 2, B.SC_STORE_F16: 4, B.SC_STORE_BF16: 4}
 

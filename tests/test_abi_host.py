@@ -47,7 +47,7 @@ def test_workspace_bytes_layout(B):
     dict(shape=(4, 4, 4), G=float("inf")),
     dict(shape=(64, 4, 4), stages=3),
     dict(shape=(64, 4, 4), tile_y=4, blocks_per_sm=1),
-    dict(shape=(64, 4, 4), tile_y=8, blocks_per_sm=3),
+    dict(shape=(64, 4, 4), tile_y=8, stages=2, blocks_per_sm=3),
     dict(shape=(64, 4, 4), tile_y=16, blocks_per_sm=2),
     dict(shape=(64, 4, 4), tile_y=16, stages=2),           # two 32 x 16 FP32 stages do not fit
     dict(shape=(33, 4, 4), tile_y=16),                      # generic kernel (odd nx in FP32): no tile_y 16
