@@ -106,6 +106,25 @@ def test_fp32_step_matches_oracle(B, shape, lattice, stencil, psi, G_self):
     assert rel(sim.populations().cpu().numpy(), ref) < 1e-6
 
 
+@pytest.mark.parametrize("shape,lattice,stencil,psi,G_self", CASES)
+@pytest.mark.parametrize("storage", ["F64", "F32"])
+def test_tau_one_step_matches_oracle(B, shape, lattice, stencil, psi, G_self, storage):
+    """tau_A = tau_B = 1: the kernels' instantiation that carries a site's momentum sums instead of its
+    populations from its density sum to its collision (generic, staged, E4, E6, D2Q9) against the
+    oracle, at the tolerances of the general form (FP64 1e-13, FP32 1e-6 and FP32_U_REL)."""
+    st = getattr(B, f"SC_STORE_{storage}")
+    sim, op, nA0, nB0 = setup(B, shape, st, lattice, stencil, psi, tau=(1.0, 1.0), G_self=G_self)
+    sim.step(12)
+    sim.sync()
+    ref = oracle.step(op, oracle.init(op, nA0, nB0), 12)
+    nA, nB, u = sim.moments()
+    oA, oB, ou = oracle.moments(op, ref)
+    tol = 1e-13 if storage == "F64" else 1e-6
+    assert rel(sim.populations().cpu().numpy(), ref) < tol
+    assert rel(nA.cpu(), oA) < tol and rel(nB.cpu(), oB) < tol
+    assert rel(u.cpu().numpy(), ou) < (1e-12 if storage == "F64" else FP32_U_REL)
+
+
 def test_config1_d2q9_2000_steps(B):
     """The 64x64 D2Q9 droplet workload (G c_s^2 = 1.4, psi = n, tau = 1), 2000
     steps, FP64 and FP32 storage against the FP64 oracle.  The minority density
