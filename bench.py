@@ -418,12 +418,15 @@ def sweep_droplets():
     return out
 
 
-BATCH_CANDIDATES = [(8, 64, 1, 3), (8, 64, 1, 2), (4, 32, 1, 3), (4, 64, 1, 3), (4, 128, 1, 3), (4, 64, 2, 2)]
+BATCH_CANDIDATES = [(8, 64, 1, 3), (8, 32, 1, 3), (8, 64, 1, 2), (4, 32, 1, 3), (4, 64, 1, 3), (4, 128, 1, 3),
+                    (4, 64, 2, 2)]
 
 
 def batch_block(B, dev, stream, plain_mlups, steps=128):
-    """Throughput of the batched radius sweep (one launch per step, CUDA graph) in FP32, FP16 and BF16
-    storage; (tile_y, tile_z, stages, blocks_per_sm) chosen by the autotuner on the whole batch."""
+    """Throughput of the batched radius sweep in FP32, FP16 and BF16 storage; (tile_y, tile_z, stages,
+    blocks_per_sm) and the launch form of whole 32-step runs (one persistent launch, or one launch per
+    step from a CUDA graph) chosen by the autotuner on the whole batch; both forms of the chosen block
+    shape are reported."""
     import torch
 
     from paper_2112_02574_gb300 import tune
@@ -435,20 +438,33 @@ def batch_block(B, dev, stream, plain_mlups, steps=128):
     for name, code in (("f32", B.SC_STORE_F32), ("f16", B.SC_STORE_F16), ("bf16", B.SC_STORE_BF16)):
         plist = [B.make_params((L, L, L), lattice=B.SC_D3Q19, psi_self=B.SC_PSI_EXP, storage=code, G=G_CROSS,
                                G_self=gs) for L, _, gs, _ in drops]
-        cfg, _, table = tune.tune_batch(plist, fields_, BATCH_CANDIDATES, steps=16, device=dev)
+        cfg, _, table = tune.tune_batch(plist, fields_, BATCH_CANDIDATES, steps=32, device=dev)
         plist = [tune.with_config(p, cfg) for p in plist]
-        with torch.cuda.stream(stream):
-            batch = B.Batch(plist, fields_, device=dev, stream=stream)
+
+        def timed(batch):
             batch.step(64)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             batch.step(steps)
             b.record(stream)
             b.synchronize()
-        ms = a.elapsed_time(b)
+            for m in batch.members:
+                m.sync()
+            return a.elapsed_time(b)
+
+        with torch.cuda.stream(stream):
+            batch = B.Batch(plist, fields_, device=dev, stream=stream)
+            forms = {}
+            if batch.persistent:  # both launch forms of the tuned block shape
+                for persistent in (True, False):
+                    batch.persistent = persistent
+                    forms["persistent" if persistent else "per_step"] = timed(batch) / steps
+            batch.persistent = cfg[4]
+            ms = timed(batch)
         mlups = sites * steps / (ms * 1e-3) / 1e6
-        res[name] = {"MLUPS": mlups, "ms_per_step": ms / steps, "staged": batch.staged,
-                     "config": dict(zip(("tile_y", "tile_z", "stages", "blocks_per_sm"), cfg)),
+        res[name] = {"MLUPS": mlups, "ms_per_step": ms / steps, "staged": batch.staged, "persistent": cfg[4],
+                     "ms_per_step_by_launch_form": forms,
+                     "config": dict(zip(("tile_y", "tile_z", "stages", "blocks_per_sm", "persistent"), cfg)),
                      "vs_plain_f32": mlups / plain_mlups if plain_mlups else None,
                      "tuning": [[list(c), round(m, 4)] for c, m in table]}
         del batch

@@ -292,15 +292,20 @@ sc_status sc_run_host_sigma(const sc_params *params, const double *nA0, const do
                            const double centre[3], double bin_width, int32_t nbins, double *nA, double *nB,
                            double *result, void *workspace, size_t ws_bytes, void *stream);
 
-/* ---- batches: several lattices stepped by one kernel launch per step ----
+/* ---- batches: several lattices stepped together ----
  * The batched radius sweep: lattices of different sizes and parameters (same
- * lattice type, stencil, storage and tile_y) stepped together; every time step
- * is ONE launch of a step kernel over a work list of (lattice, tile) items,
- * replayed from a CUDA graph of 32 chained launches (built explicitly, no
- * stream capture).  The kernel is the staged one when every member can take it
+ * lattice type, stencil, storage and tile_y) stepped together over a work list
+ * of (lattice, tile) items, from a CUDA graph (built explicitly, no stream
+ * capture).  The kernel is the staged one when every member can take it
  * (variant 0 or 2, D3Q19, E4, nx >= 32 a multiple of the chunk sites; members
  * then share stages and blocks_per_sm), else the generic one; a member with
- * variant 2 in a batch that cannot be staged is an error (SC_EINVAL).  Each member is an ordinary context for the analysis
+ * variant 2 in a batch that cannot be staged is an error (SC_EINVAL).
+ * A staged batch runs 32 time steps of every member in ONE persistent
+ * cooperative launch (its blocks take the work items of a step and meet at a
+ * grid-wide barrier before the next; a barrier wait that runs out sets bit 1 of
+ * every member's status word, reported by sc_sync as SC_ETIMEOUT); a generic
+ * batch replays 32 chained launches, one per step.  Steps outside whole runs of
+ * 32 are single launches.  Each member is an ordinary context for the analysis
  * entry points (sc_moments, sc_pressure_profile, sc_bulk_pressure_at, ...);
  * sc_step refuses batch members. */
 typedef struct sc_batch sc_batch;
@@ -312,11 +317,19 @@ sc_status sc_batch_create(int32_t n, const sc_params *params, const double *cons
                           void *workspace, size_t ws_bytes, void *stream, sc_batch **out);
 /* Advance every member by nsteps time steps (section 2); asynchronous. */
 sc_status sc_batch_step(sc_batch *batch, int64_t nsteps);
+/* Choose how whole runs of 32 steps of a staged batch go out: on = 1 (the
+ * default where the device has cooperative launch) one persistent launch per
+ * run, on = 0 one launch per step.  Both forms give the same members bit for
+ * bit.  Waits for the batch's stream.  SC_EUNSUPPORTED for on = 1 when the
+ * batch has no persistent form (a generic batch, or no cooperative launch). */
+sc_status sc_batch_set_persistent(sc_batch *batch, int32_t on);
 /* Member k as a context (owned by the batch; NULL if k is out of range). */
 sc_ctx *sc_batch_member(sc_batch *batch, int32_t k);
-/* Batched step launches issued so far (each steps every member once). */
+/* Time steps issued to every member so far (a persistent launch counts once
+ * per step it runs). */
 int64_t sc_batch_launches(const sc_batch *batch);
-/* Step kernel of the batch: 1 generic, 2 staged (0 for NULL). */
+/* Step kernel of the batch: 1 generic, 2 staged (one launch per step), 3 staged
+ * and persistent (0 for NULL). */
 int32_t sc_batch_variant(const sc_batch *batch);
 /* Stop stepping member k (section 4 runs each droplet until it has converged,
  * so members of a sweep finish at different times).  The member keeps its state

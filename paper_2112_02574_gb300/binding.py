@@ -91,6 +91,7 @@ def _load():
         "sc_batch_variant": (I32, [V]),
         "sc_batch_retire": (I32, [V, I32]),
         "sc_batch_active": (I32, [V]),
+        "sc_batch_set_persistent": (I32, [V, I32]),
         "sc_velocity_change": (I32, [V, V, V]),
         "sc_centre_of_mass": (I32, [V, I32, D, V]),
         "sc_batch_destroy": (None, [V]),
@@ -281,6 +282,10 @@ def sc_batch_active(batch) -> int:
     return lib.sc_batch_active(batch)
 
 
+def sc_batch_set_persistent(batch, on: bool):
+    _check(lib.sc_batch_set_persistent(batch, int(bool(on))))
+
+
 def sc_velocity_change(ctx, u_prev, out):
     _check(lib.sc_velocity_change(ctx, _ptr(u_prev), _ptr(out)))
 
@@ -439,7 +444,8 @@ class _Member(Simulation):
 
 
 class Batch:
-    """Several lattices stepped together: one kernel launch per time step."""
+    """Several lattices stepped together: one kernel launch per time step, or one
+    persistent launch per 32 steps for a staged batch."""
 
     def __init__(self, params_list, fields, device="cuda", stream=None):
         self.params = list(params_list)
@@ -471,7 +477,16 @@ class Batch:
     @property
     def staged(self) -> bool:
         """True when the batch steps with the staged kernel."""
-        return sc_batch_variant(self.handle) == 2
+        return sc_batch_variant(self.handle) >= 2
+
+    @property
+    def persistent(self) -> bool:
+        """True when 32-step runs go out as one persistent cooperative launch."""
+        return sc_batch_variant(self.handle) == 3
+
+    @persistent.setter
+    def persistent(self, on: bool):
+        sc_batch_set_persistent(self.handle, on)
 
     def retire(self, k: int):
         """Stop stepping member k (it keeps its state for analysis)."""

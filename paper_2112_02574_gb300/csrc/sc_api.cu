@@ -256,6 +256,14 @@ struct sc_batch {
   int active;         // members still stepped
   const void *kernel;
   size_t smem;
+  // the persistent form of the staged batch (one cooperative launch runs kGraphSteps steps of every
+  // member; nullptr when the batch is not staged or the device has no cooperative launch)
+  const void *pkernel;
+  size_t psmem;
+  int pgrid;           // blocks of a persistent launch: the work items, at most the co-resident blocks
+  unsigned *counter;   // its grid-barrier counter and kGraphSteps ticket counters (device, zeroed
+                       // before every launch)
+  int persist_off;     // per-step launches requested (sc_batch_set_persistent(b, 0))
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   int64_t steps, launches;
@@ -915,6 +923,8 @@ sc_status sc_sync(sc_ctx *c) {
   SC_CUDA(cudaMemcpy(&w, status_word(c), sizeof(w), cudaMemcpyDeviceToHost));
   if (w) {
     SC_CUDA(cudaMemset(status_word(c), 0, sizeof(unsigned int)));
+    if (w & 2u)
+      return fail(SC_ETIMEOUT, "a bounded device-side wait of a step kernel ran out (status 0x%x)", w);
     return fail(SC_ENAN, "a time step met a non-finite density, or a non-positive one with psi = exp(-1/n) "
                          "(status 0x%x)", w);
   }
@@ -985,6 +995,7 @@ sc_status sc_run_host_sigma(const sc_params *params, const double *nA0, const do
 // ------------------------------------------------------------------ batches
 namespace {
 constexpr int kGraphSteps = 32;  // steps per graph replay (even: parity preserved)
+static_assert(sizeof(unsigned) * (1 + kGraphSteps) <= kAlign, "the batch's counters fit in one aligned slot");
 
 // A batch steps every member with the staged kernel when all of them can take
 // it (and none asks for the generic one), else every member with the generic kernel.
@@ -1023,7 +1034,7 @@ size_t batch_table_bytes(int32_t n, const sc_params *params, int *nitems_out) {
     nitems += ((q.nx + 31) / 32) * ((q.ny + ty - 1) / ty) * ((q.nz + tz - 1) / tz);
   }
   if (nitems_out) *nitems_out = nitems;
-  return align_up(sizeof(StepArgs<double>) * (size_t)n) + align_up(sizeof(int4) * (size_t)nitems);
+  return align_up(sizeof(StepArgs<double>) * (size_t)n) + align_up(sizeof(int4) * (size_t)nitems) + kAlign;
 }
 
 sc_status batch_validate(int32_t n, const sc_params *params) {
@@ -1082,14 +1093,76 @@ sc_status batch_upload_items(sc_batch *b) {
   return SC_OK;
 }
 
-// A graph of kGraphSteps chained launches over the current work list, swap = 0, 1, 0, 1, ...
-// (none when no member is left).
+// The persistent form: a graph of two nodes, the barrier and ticket counters zeroed, then one
+// cooperative launch of the persistent kernel running kGraphSteps steps from swap 0, with as many
+// blocks as there are work items but at most the co-resident blocks of the device.  False (nothing built) when the
+// device cannot hold a useful grid.
+bool batch_build_persistent(sc_batch *b) {
+  int dev = 0, sms = 0, occ = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, b->pkernel, 32 * b->tile_y, b->psmem) != cudaSuccess ||
+      occ < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  b->pgrid = b->nitems < sms * occ ? b->nitems : sms * occ;
+  cudaError_t e = cudaGraphCreate(&b->graph, 0);
+  cudaGraphNode_t zero = nullptr, node = nullptr;
+  if (e == cudaSuccess) {
+    cudaMemsetParams mp;
+    memset(&mp, 0, sizeof(mp));
+    mp.dst = b->counter;
+    mp.value = 0;
+    mp.elementSize = sizeof(unsigned);
+    mp.width = 1 + kGraphSteps;  // the barrier counter and one ticket counter per step
+    mp.height = 1;
+    e = cudaGraphAddMemsetNode(&zero, b->graph, nullptr, 0, &mp);
+  }
+  void *argp = b->args_dev;
+  void *itemp = b->items_dev;
+  int nitems = b->nitems, nsteps = kGraphSteps, swap0 = 0, nlat = b->n;
+  unsigned *counter = b->counter;
+  void *kp[7] = {&argp, &itemp, &nitems, &nsteps, &swap0, &counter, &nlat};
+  if (e == cudaSuccess) {
+    cudaKernelNodeParams np;
+    memset(&np, 0, sizeof(np));
+    np.func = const_cast<void *>(b->pkernel);
+    np.gridDim = dim3(b->pgrid);
+    np.blockDim = dim3(32, b->tile_y);
+    np.sharedMemBytes = (unsigned)b->psmem;
+    np.kernelParams = kp;
+    e = cudaGraphAddKernelNode(&node, b->graph, &zero, 1, &np);
+  }
+  if (e == cudaSuccess) {
+    cudaLaunchAttributeValue v;
+    memset(&v, 0, sizeof(v));
+    v.cooperative = 1;
+    e = cudaGraphKernelNodeSetAttribute(node, cudaLaunchAttributeCooperative, &v);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (e != cudaSuccess) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->pgrid = 0;
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
+// A graph of kGraphSteps steps over the current work list, swap = 0, 1, 0, 1, ...: the persistent
+// form where the batch has one, else kGraphSteps chained launches (none when no member is left).
 sc_status batch_build_graph(sc_batch *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   b->exec = nullptr;
   b->graph = nullptr;
+  b->pgrid = 0;
   if (b->nitems == 0) return SC_OK;
+  if (b->pkernel && !b->persist_off && batch_build_persistent(b)) return SC_OK;
   cudaError_t e = cudaGraphCreate(&b->graph, 0);
   cudaGraphNode_t prev = nullptr;
   int swaps[2] = {0, 1};
@@ -1164,6 +1237,8 @@ sc_status sc_batch_create(int32_t n, const sc_params *params, const double *cons
   b->args_dev = ws + off;
   off += align_up(sizeof(StepArgs<double>) * (size_t)n);
   b->items_dev = reinterpret_cast<int4 *>(ws + off);
+  off += align_up(sizeof(int4) * (size_t)nitems);
+  b->counter = reinterpret_cast<unsigned *>(ws + off);
   const int storage = params[0].storage;
   const size_t arg_size = storage == SC_STORE_F64 ? sizeof(StepArgs<double>) : sizeof(StepArgs<float>);
   std::string host_args(arg_size * n, '\0');
@@ -1214,6 +1289,17 @@ sc_status sc_batch_create(int32_t n, const sc_params *params, const double *cons
       case SC_STORE_BF16: b->kernel = batched_staged_kernel_bf16(b->tile_y, ns, mb, any_self, all_t1, &b->smem); break;
       default: b->kernel = batched_staged_kernel_f64(b->tile_y, ns, mb, any_self, all_t1, &b->smem); break;
     }
+    int dev = 0, coop = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop) {
+      switch (storage) {
+        case SC_STORE_F32: b->pkernel = persistent_staged_kernel_f32(b->tile_y, ns, mb, any_self, all_t1, &b->psmem); break;
+        case SC_STORE_F16: b->pkernel = persistent_staged_kernel_f16(b->tile_y, ns, mb, any_self, all_t1, &b->psmem); break;
+        case SC_STORE_BF16: b->pkernel = persistent_staged_kernel_bf16(b->tile_y, ns, mb, any_self, all_t1, &b->psmem); break;
+        default: b->pkernel = persistent_staged_kernel_f64(b->tile_y, ns, mb, any_self, all_t1, &b->psmem); break;
+      }
+    }
+    cudaGetLastError();  // a configuration without a persistent form leaves the per-step launches
   } else {
     switch (storage) {
       case SC_STORE_F32: b->kernel = batched_kernel_f32(lat, sten, b->tile_y, all_t1, &b->smem); break;
@@ -1285,6 +1371,18 @@ sc_status sc_batch_retire(sc_batch *b, int32_t k) {
 
 int32_t sc_batch_active(const sc_batch *b) { return b ? b->active : 0; }
 
+sc_status sc_batch_set_persistent(sc_batch *b, int32_t on) {
+  if (!b) return fail(SC_EINVAL, "batch is NULL");
+  if (on != 0 && on != 1) return fail(SC_EINVAL, "on must be 0 or 1");
+  if (on && !b->pkernel) return fail(SC_EUNSUPPORTED, "the batch has no persistent form (generic kernel or no cooperative launch)");
+  SC_CUDA(cudaStreamSynchronize(b->stream));
+  b->persist_off = !on;
+  sc_status st = batch_build_graph(b);
+  if (st == SC_OK && on && b->nitems > 0 && b->pgrid == 0)
+    return fail(SC_EUNSUPPORTED, "the persistent launch could not be built on this device");
+  return st;
+}
+
 sc_ctx *sc_batch_member(sc_batch *b, int32_t k) {
   if (!b || k < 0 || k >= b->n) {
     fail(SC_EINVAL, "no such batch member");
@@ -1294,7 +1392,7 @@ sc_ctx *sc_batch_member(sc_batch *b, int32_t k) {
 }
 
 int64_t sc_batch_launches(const sc_batch *b) { return b ? b->launches : 0; }
-int32_t sc_batch_variant(const sc_batch *b) { return b ? (b->staged ? 2 : 1) : 0; }
+int32_t sc_batch_variant(const sc_batch *b) { return b ? (b->staged ? (b->pgrid > 0 ? 3 : 2) : 1) : 0; }
 
 void sc_batch_destroy(sc_batch *b) {
   if (!b) return;

@@ -60,4 +60,17 @@ const void *batched_staged_kernel_bf16(int tile_y, int stages, int blocks_per_sm
 const void *batched_staged_kernel_f64(int tile_y, int stages, int blocks_per_sm, bool self_on, bool t1,
                                          size_t *smem);
 
+// The persistent batched staged step kernel (D3Q19, E4), same configurations: parameters
+// (const StepArgs *args, const int4 *items, int nitems, int nsteps, int swap0, unsigned *counter,
+// int nlat), block (32, tile_y), launched cooperatively with at most the co-resident blocks;
+// nullptr if not instantiated.
+const void *persistent_staged_kernel_f32(int tile_y, int stages, int blocks_per_sm, bool self_on, bool t1,
+                                         size_t *smem);
+const void *persistent_staged_kernel_f16(int tile_y, int stages, int blocks_per_sm, bool self_on, bool t1,
+                                         size_t *smem);
+const void *persistent_staged_kernel_bf16(int tile_y, int stages, int blocks_per_sm, bool self_on, bool t1,
+                                          size_t *smem);
+const void *persistent_staged_kernel_f64(int tile_y, int stages, int blocks_per_sm, bool self_on, bool t1,
+                                         size_t *smem);
+
 }  // namespace scgb

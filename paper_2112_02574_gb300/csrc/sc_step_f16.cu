@@ -15,3 +15,7 @@ cudaError_t scgb::staged_occupancy_f16(int tile_y, int stages, int blocks_per_sm
 cudaError_t scgb::generic_occupancy_f16(int lattice, int stencil, int tile_y, bool t1, int *blocks) {
   return generic_occupancy<__half, float>(lattice, stencil, tile_y, t1, blocks);
 }
+const void *scgb::persistent_staged_kernel_f16(int tile_y, int stages, int blocks_per_sm, bool self_on, bool t1,
+                                              size_t *smem) {
+  return persistent_staged_any<__half, float>(tile_y, stages, blocks_per_sm, self_on, t1, smem);
+}

@@ -203,6 +203,26 @@ const void *batched_staged_one(bool self_on, bool t1, size_t *smem) {
   return reinterpret_cast<const void *>(k);
 }
 
+template <class ST, class CT, int TY, int NS, int MINB>
+const void *persistent_staged_one(bool self_on, bool t1, size_t *smem) {
+  auto *k = t1 ? sc_step_staged_persistent<ST, CT, TY, NS, MINB, true>
+               : sc_step_staged_persistent<ST, CT, TY, NS, MINB, false>;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(staged_smem_bytes<ST, CT, TY, NS>())) != cudaSuccess)
+    return nullptr;
+  *smem = staged_smem_bytes<ST, CT, TY, NS>(self_on);
+  return reinterpret_cast<const void *>(k);
+}
+
+// Same configurations as launch_staged.
+template <class ST, class CT>
+const void *persistent_staged_any(int ty, int ns, int mb, bool self_on, bool t1, size_t *smem) {
+  return with_staged_cfg<ST>(ty, ns, mb, static_cast<const void *>(nullptr), [&](auto cfg) {
+    using C = decltype(cfg);
+    return persistent_staged_one<ST, CT, C::TY, C::NS, C::MINB>(self_on, t1, smem);
+  });
+}
+
 // Same configurations as launch_staged.
 template <class ST, class CT>
 const void *batched_staged_any(int ty, int ns, int mb, bool self_on, bool t1, size_t *smem) {

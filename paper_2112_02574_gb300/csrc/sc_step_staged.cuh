@@ -361,4 +361,94 @@ __global__ void __launch_bounds__(32 * TY, MINB)
   staged_block<ST, CT, TY, NS, T1>(s_a, it.y, it.z, z0, min(z0 + s_a.tile_z, s_a.nz), false, smem_raw);
 }
 
+// Grid-wide barrier between the time steps of a persistent launch (all blocks co-resident: the
+// launch is cooperative).  Each block arrives once per step on a counter that starts at zero for
+// the launch and waits until all gridDim.x blocks have arrived for step t (target (t + 1) gridDim.x).
+// The block's stores of the step are made visible device-wide before it arrives; the next step reads
+// them through L2 only (cp.async.cg).  The wait is bounded: false when it ran out.
+__device__ __forceinline__ bool grid_step_barrier(unsigned *counter, unsigned target) {
+  __syncthreads();
+  int ok = 1;
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    __threadfence();
+    atomicAdd(counter, 1u);
+    // polls back off from 64 ns to 4 us (a step takes milliseconds): the waiting blocks keep the L2
+    // slice of the counter free for the blocks still working; at most 2^20 polls (a few seconds)
+    unsigned spins = 0, pause = 64;
+    while (*reinterpret_cast<volatile unsigned *>(counter) < target) {
+      if (++spins > (1u << 20)) {
+        ok = 0;
+        break;
+      }
+      __nanosleep(pause);
+      pause = pause < 4096 ? 2 * pause : pause;
+    }
+    __threadfence();
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+// One work item of the persistent launch, compiled as its own function so that its register
+// allocation is the one of a single-item block (inlined into the item loop the compiler keeps more
+// values live across items); one copy per kernel (MINB), each under that kernel's register limit.
+template <class ST, class CT, int TY, int NS, int MINB, bool T1>
+__device__ __noinline__ void staged_item(const StepArgs<CT> &a, int bx, int by, int z0, int zend,
+                                         unsigned char *smem_raw) {
+  staged_block<ST, CT, TY, NS, T1>(a, bx, by, z0, zend, false, smem_raw);
+}
+
+// Persistent form of the batched staged step: one cooperative launch runs nsteps time steps of every
+// lattice of the batch.  In step t the blocks draw work items (the same list as the per-step launch)
+// from the ticket counter counter[1 + t] until the list is exhausted, so that, as with the hardware's
+// block dispatch of a per-step launch, a block that finishes early takes the next item; then all meet
+// at the grid barrier (counter[0]) before step t + 1.  Step t swaps source and destination when
+// (swap0 + t) is odd.  counter[0 .. nsteps] start at zero.  A barrier that runs out sets bit 1 of every
+// lattice's status word and ends the launch.
+template <class ST, class CT, int TY, int NS, int MINB, bool T1>
+__global__ void __launch_bounds__(32 * TY, MINB)
+    sc_step_staged_persistent(const StepArgs<CT> *__restrict__ args, const int4 *__restrict__ items, int nitems,
+                              int nsteps, int swap0, unsigned *counter, int nlat) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ StepArgs<CT> s_a;
+  __shared__ int4 s_it;  // the block's current item; x = -1 when step s_it.y's list is exhausted
+  __shared__ int s_t;    // the block's current step
+  if (threadIdx.x == 0 && threadIdx.y == 0) s_t = 0;
+  for (;;) {
+    __syncthreads();  // the previous item is done with the shared arguments, tables and rings
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      const int t = s_t;
+      const int w = (int)atomicAdd(counter + 1 + t, 1u);
+      int4 it = make_int4(-1, t, 0, 0);
+      if (w < nitems) {
+        it = items[w];
+        StepArgs<CT> a = args[it.x];
+        if ((swap0 + t) & 1) {
+          const void *u = a.src;
+          a.src = a.dst;
+          a.dst = const_cast<void *>(u);
+          const float2 *v = a.nsrc;
+          a.nsrc = a.ndst;
+          a.ndst = const_cast<float2 *>(v);
+        }
+        s_a = a;
+      }
+      s_it = it;
+    }
+    __syncthreads();
+    if (s_it.x >= 0) {
+      const int z0 = s_it.w * s_a.tile_z;
+      staged_item<ST, CT, TY, NS, MINB, T1>(s_a, s_it.y, s_it.z, z0, min(z0 + s_a.tile_z, s_a.nz), smem_raw);
+      continue;
+    }
+    const int t = s_it.y;  // step t is exhausted: wait for every block, then take step t + 1
+    if (t + 1 >= nsteps) return;
+    if (!grid_step_barrier(counter, unsigned(t + 1) * gridDim.x)) {
+      if (threadIdx.x == 0 && threadIdx.y == 0)
+        for (int k = 0; k < nlat; ++k) atomicOr(args[k].err, 2u);
+      return;
+    }
+    if (threadIdx.x == 0 && threadIdx.y == 0) s_t = t + 1;
+  }
+}
+
 }  // namespace scgb

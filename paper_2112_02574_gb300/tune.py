@@ -63,26 +63,30 @@ def tune_step(params, nA0, nB0, candidates=None, steps: int = 64, warmup: int = 
 
 
 def with_config(p, cfg):
-    """Copy of sc_params p with (tile_y, tile_z, stages, blocks_per_sm) = cfg."""
-    ty, tz, ns, mb = cfg
+    """Copy of sc_params p with (tile_y, tile_z, stages, blocks_per_sm) = cfg[:4]."""
+    ty, tz, ns, mb = cfg[:4]
     return B.make_params((p.nx, p.ny, p.nz), lattice=p.lattice, stencil=p.stencil, psi_self=p.psi_self,
                          storage=p.storage, tau=tuple(p.tau), G=p.G, G_self=tuple(p.G_self), tile_y=ty, tile_z=tz,
                          variant=p.variant, stages=ns, blocks_per_sm=mb)
 
 
 def tune_batch(params_list, fields, candidates, steps: int = 32, device="cuda"):
-    """(tile_y, tile_z, stages, blocks_per_sm) for a batch (shared by its members), timed on the
-    whole batch.  Returns (best, ms_per_step, table)."""
+    """(tile_y, tile_z, stages, blocks_per_sm, persistent) for a batch (shared by its members), timed on
+    the whole batch: each candidate block shape with whole 32-step runs as one persistent launch (where
+    the batch has that form) and as one launch per step (steps a multiple of 32 times the graph
+    replays).  Returns (best, ms_per_step, table)."""
     table = []
     for cfg in candidates:
         batch = B.Batch([with_config(p, cfg) for p in params_list], fields, device=device)
-        batch.step(4)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(batch.stream)
-        batch.step(steps)
-        b.record(batch.stream)
-        b.synchronize()
-        table.append((tuple(cfg), a.elapsed_time(b) / steps))
+        for persistent in ((True, False) if batch.persistent else (False,)):
+            batch.persistent = persistent
+            batch.step(4)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(batch.stream)
+            batch.step(steps)
+            b.record(batch.stream)
+            b.synchronize()
+            table.append((tuple(cfg) + (persistent,), a.elapsed_time(b) / steps))
         del batch
     best = min(table, key=lambda t: t[1])
     return best[0], best[1], table

@@ -1,5 +1,6 @@
 """The batched radius sweep: lattices of uneven sizes and parameters stepped
-together by one launch per time step (replayed from a CUDA graph).  Each
+together, one launch per time step (replayed from a CUDA graph) or, for the
+staged kernel, one persistent launch per 32 steps.  Each
 member must match the same lattice stepped on its own, bit for bit (same
 kernel body and arithmetic), and the FP64 member must match the oracle."""
 import numpy as np
@@ -66,7 +67,7 @@ def test_staged_batch_members_equal_single_runs(B, storage):
         f = S.droplet((L, L, L), (L // 2,) * 3, R, n_in=0.85, n_out=0.15, amplitude=1e-3, seed=200 + k)
         sets.append((p, f, kw, L))
     batch = B.Batch([s_[0] for s_ in sets], [s_[1] for s_ in sets])
-    assert batch.staged
+    assert batch.staged and batch.persistent
     batch.step(37)
     for (p, f, kw, L), m in zip(sets, batch.members):
         single = B.Simulation(B.make_params((L, L, L), lattice=B.SC_D3Q19, psi_self=B.SC_PSI_EXP, storage=st,
@@ -117,3 +118,39 @@ def test_staged_batch_fp64_member_matches_oracle(B):
         ref = oracle.step(op, oracle.init(op, *f), 12)
         got = m.populations().cpu().numpy()
         assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("storage", ["F32", "BF16"])
+def test_persistent_batch_equals_per_step_launches(B, storage):
+    """More work items than co-resident blocks (tile_z 2: 800 items), so each block
+    of the persistent launch takes several items per step.  The batch run as
+    persistent launches (tile 32 x 8, one stage, two blocks per SM) equals the same batch run one launch
+    per step bit for bit
+    (single steps, then whole 32-step runs from an even step, then single steps),
+    and member 0 equals a lone run; member 1 has tau != 1 (the general collision)."""
+    st = getattr(B, f"SC_STORE_{storage}")
+    sets = []
+    for k, L in enumerate((64, 48)):
+        kw = dict(G=2.5, G_self=(0.0, 0.0) if k == 0 else (-0.4, 0.0), tau=(1.0, 1.0) if k == 0 else (0.9, 1.0))
+        f = S.droplet((L, L, L), (L // 2,) * 3, L / 4, n_in=0.85, n_out=0.15, amplitude=1e-3, seed=500 + k)
+        sets.append((B.make_params((L, L, L), lattice=B.SC_D3Q19, psi_self=B.SC_PSI_EXP, storage=st, tile_y=8,
+                                   tile_z=2, stages=1, blocks_per_sm=2, **kw), f, kw, L))
+    states = []
+    for persistent in (True, False):
+        batch = B.Batch([x[0] for x in sets], [x[1] for x in sets])
+        assert batch.staged
+        batch.persistent = persistent
+        assert batch.persistent == persistent
+        batch.step(3)
+        batch.step(66)
+        assert batch.launches == 69
+        for m in batch.members:
+            m.sync()  # a status word with a timed-out barrier raises here
+        states.append([m.state().cpu().numpy() for m in batch.members])
+    for a, b in zip(*states):
+        np.testing.assert_array_equal(a, b)
+    p, f, kw, L = sets[0]
+    lone = B.Simulation(B.make_params((L, L, L), lattice=B.SC_D3Q19, psi_self=B.SC_PSI_EXP, storage=st, tile_z=16,
+                                      variant=1, **kw), *f)
+    lone.step(69)
+    np.testing.assert_array_equal(states[0][0], lone.state().cpu().numpy())
