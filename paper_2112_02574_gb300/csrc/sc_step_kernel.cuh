@@ -33,12 +33,6 @@ __device__ __forceinline__ P2<CT> wpair(int i, P2<CT> scale) {
   if constexpr (scaled_units<ST>()) return pmul(pbc(CT(Lattice<LAT>::w(i))), scale);
   return pbc(CT(Lattice<LAT>::w(i)));
 }
-// -w_i likewise.
-template <int LAT, class ST, class CT>
-__device__ __forceinline__ P2<CT> wpair_neg(int i, P2<CT> scale) {
-  if constexpr (scaled_units<ST>()) return pmul(pbc(CT(-Lattice<LAT>::w(i))), scale);
-  return pbc(CT(-Lattice<LAT>::w(i)));
-}
 // A sum of pairs in the step's units, as a natural value.
 template <class ST, class CT>
 __device__ __forceinline__ P2<CT> unscale(P2<CT> v, P2<CT> inv_scale) {
@@ -207,8 +201,11 @@ __device__ __forceinline__ void collide_pair(const StepArgs<CT> &a, const P2<CT>
   const P2<CT> om = a.omega, ga = a.guo;
   const CT uu = rfma(u[2], u[2], rfma(u[1], u[1], rmul(u[0], u[0])));
   const P2<CT> uF = pfma(pbc(u[2]), F[2], pfma(pbc(u[1]), F[1], pmul(pbc(u[0]), F[0])));
-  const P2<CT> a0 =
-      pfma(pmul(pbc(CT(-3)), ga), uF, pfma(pmul(pmul(pbc(CT(-1.5)), om), n), pbc(uu), pmul(om, dn)));
+  // with a local reference the stored value is out_i - w_i dn (see store_pairs): the - dn is taken
+  // into a0 here, (omega - 1) dn in place of omega dn (zero for tau = 1)
+  const P2<CT> a0 = pfma(pmul(pbc(CT(-3)), ga), uF,
+                         pfma(pmul(pmul(pbc(CT(-1.5)), om), n), pbc(uu),
+                              pmul(local_ref<ST>() ? psub(om, pbc(CT(1))) : om, dn)));
   const P2<CT> a1 = pmul(pmul(pbc(CT(3)), om), n), a2 = pmul(pmul(pbc(CT(4.5)), om), n);
   const P2<CT> a3 = pmul(pbc(CT(9)), ga), a4 = pmul(pbc(CT(3)), ga);
   const P2<CT> keep = psub(pbc(CT(1)), om);
@@ -247,16 +244,13 @@ __device__ __forceinline__ void check_density(const StepArgs<CT> &a, P2<CT> n) {
 
 // Store the post-collision pairs (deviations from w_i nbar).  With a local
 // reference the stored value is relative to this site's density n = nbar + dn,
-// i.e. out_i - w_i dn, and dn = n - nbar goes to ndst.
+// i.e. out_i - w_i dn (collide_pair has already subtracted w_i dn), and
+// dn = n - nbar goes to ndst.
 template <int LAT, class ST, class CT, int Q>
 __device__ __forceinline__ void store_pairs(const StepArgs<CT> &a, ST *__restrict__ dst, int64_t site,
                                             const P2<CT> (&out)[Q], P2<CT> n, P2<CT> dn) {
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    P2<CT> v = out[i];
-    if constexpr (local_ref<ST>()) v = pfma(wpair_neg<LAT, ST, CT>(i, a.scale), dn, v);
-    Codec2<ST, CT>::store(dst + ((int64_t)i * a.N + site) * 2, v, a.scale);
-  }
+  for (int i = 0; i < Q; ++i) Codec2<ST, CT>::store(dst + ((int64_t)i * a.N + site) * 2, out[i], a.scale);
   if constexpr (local_ref<ST>()) a.ndst[site] = make_float2(float(dn.x), float(dn.y));
 }
 
