@@ -271,9 +271,19 @@ sc_status sc_pressure_profile_noalloc(const sc_params *params, const double *nA,
  * momentum x, y, z) summed over the lattice (section 2).  Asynchronous. */
 sc_status sc_totals(sc_ctx *ctx, double *out);
 
-/* Wait for the context's stream and report device-side errors (SC_ENAN, see
- * sc_status; the flag is then cleared). */
+/* Wait for the context's stream and report device-side errors (SC_ENAN, or
+ * SC_ETIMEOUT for a bounded wait that ran out; see sc_status; the flag is then
+ * cleared). */
 sc_status sc_sync(sc_ctx *ctx);
+
+/* Self-test of the bounded device-side wait that a persistent batch launch
+ * uses between time steps: one block on ctx's stream waits at that grid barrier
+ * for an arrival that never comes; after max_polls polls (1 <= max_polls <=
+ * 2^20; polls back off from 64 ns to 4 us) the wait runs out and sets the
+ * timeout bit of ctx's status word, so that the next sc_sync returns
+ * SC_ETIMEOUT and clears it.  The context's state is untouched and it stays
+ * usable.  Asynchronous; SC_EINVAL for a NULL ctx or max_polls out of range. */
+sc_status sc_selftest_wait_timeout(sc_ctx *ctx, int32_t max_polls);
 
 /* Convenience entry point with HOST buffers: create, run nsteps and read the
  * densities back.  nA0, nB0: host FP64 [N] in; nA, nB: host FP64 [N] out.

@@ -92,6 +92,7 @@ def _load():
         "sc_batch_retire": (I32, [V, I32]),
         "sc_batch_active": (I32, [V]),
         "sc_batch_set_persistent": (I32, [V, I32]),
+        "sc_selftest_wait_timeout": (I32, [V, I32]),
         "sc_velocity_change": (I32, [V, V, V]),
         "sc_centre_of_mass": (I32, [V, I32, D, V]),
         "sc_batch_destroy": (None, [V]),
@@ -229,6 +230,10 @@ def sc_totals(ctx, out):
 
 def sc_sync(ctx):
     _check(lib.sc_sync(ctx))
+
+
+def sc_selftest_wait_timeout(ctx, max_polls: int):
+    _check(lib.sc_selftest_wait_timeout(ctx, int(max_polls)))
 
 
 def sc_run_host(params, nA0, nB0, nsteps, nA, nB, workspace, stream=None):

@@ -931,6 +931,15 @@ sc_status sc_sync(sc_ctx *c) {
   return SC_OK;
 }
 
+sc_status sc_selftest_wait_timeout(sc_ctx *c, int32_t max_polls) {
+  if (!c) return fail(SC_EINVAL, "ctx is NULL");
+  if (max_polls < 1 || max_polls > (1 << 20)) return fail(SC_EINVAL, "max_polls must be in [1, 2^20]");
+  // the probe's barrier counter: a word of the status area that nothing else uses
+  unsigned *counter = reinterpret_cast<unsigned *>(c->ws + c->L.off_status + 128);
+  SC_CUDA(launch_barrier_probe(counter, status_word(c), (unsigned)max_polls, c->stream));
+  return SC_OK;
+}
+
 sc_status sc_run_host(const sc_params *params, const double *nA0, const double *nB0, int64_t nsteps, double *nA,
                       double *nB, void *workspace, size_t ws_bytes, void *stream) {
   sc_status st = validate(params);

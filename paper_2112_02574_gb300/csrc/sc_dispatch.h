@@ -72,5 +72,8 @@ const void *persistent_staged_kernel_bf16(int tile_y, int stages, int blocks_per
                                           size_t *smem);
 const void *persistent_staged_kernel_f64(int tile_y, int stages, int blocks_per_sm, bool self_on, bool t1,
                                          size_t *smem);
+// Self-test of the persistent launch's bounded grid-barrier wait (one block, a barrier that never
+// completes): zeroes *counter, then the wait runs out after max_polls polls and sets bit 1 of *err.
+cudaError_t launch_barrier_probe(unsigned *counter, unsigned *err, unsigned max_polls, cudaStream_t st);
 
 }  // namespace scgb

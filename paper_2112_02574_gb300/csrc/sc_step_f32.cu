@@ -19,3 +19,13 @@ const void *scgb::persistent_staged_kernel_f32(int tile_y, int stages, int block
                                               size_t *smem) {
   return persistent_staged_any<float, float>(tile_y, stages, blocks_per_sm, self_on, t1, smem);
 }
+
+__global__ void scgb::grid_barrier_probe(unsigned *counter, unsigned *err, unsigned max_polls) {
+  if (!grid_step_barrier(counter, 2u, max_polls) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(err, 2u);
+}
+cudaError_t scgb::launch_barrier_probe(unsigned *counter, unsigned *err, unsigned max_polls, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  grid_barrier_probe<<<1, 32, 0, st>>>(counter, err, max_polls);
+  return cudaGetLastError();
+}

@@ -365,18 +365,19 @@ __global__ void __launch_bounds__(32 * TY, MINB)
 // launch is cooperative).  Each block arrives once per step on a counter that starts at zero for
 // the launch and waits until all gridDim.x blocks have arrived for step t (target (t + 1) gridDim.x).
 // The block's stores of the step are made visible device-wide before it arrives; the next step reads
-// them through L2 only (cp.async.cg).  The wait is bounded: false when it ran out.
-__device__ __forceinline__ bool grid_step_barrier(unsigned *counter, unsigned target) {
+// them through L2 only (cp.async.cg).  The wait is bounded (max_polls polls): false when it ran out.
+__device__ __forceinline__ bool grid_step_barrier(unsigned *counter, unsigned target,
+                                                  unsigned max_polls = 1u << 20) {
   __syncthreads();
   int ok = 1;
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     __threadfence();
     atomicAdd(counter, 1u);
     // polls back off from 64 ns to 4 us (a step takes milliseconds): the waiting blocks keep the L2
-    // slice of the counter free for the blocks still working; at most 2^20 polls (a few seconds)
+    // slice of the counter free for the blocks still working; 2^20 polls take a few seconds
     unsigned spins = 0, pause = 64;
     while (*reinterpret_cast<volatile unsigned *>(counter) < target) {
-      if (++spins > (1u << 20)) {
+      if (++spins > max_polls) {
         ok = 0;
         break;
       }
@@ -387,6 +388,11 @@ __device__ __forceinline__ bool grid_step_barrier(unsigned *counter, unsigned ta
   }
   return __syncthreads_and(ok) != 0;
 }
+
+// Self-test of the bounded wait: one block waits at the grid barrier for two arrivals of which only
+// its own ever comes, so the wait runs out after max_polls polls and, as in a persistent launch, bit 1
+// of *err is set.  *counter must be zero.
+__global__ void grid_barrier_probe(unsigned *counter, unsigned *err, unsigned max_polls);
 
 // One work item of the persistent launch, compiled as its own function so that its register
 // allocation is the one of a single-item block (inlined into the item loop the compiler keeps more

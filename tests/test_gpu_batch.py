@@ -154,3 +154,25 @@ def test_persistent_batch_equals_per_step_launches(B, storage):
                                       variant=1, **kw), *f)
     lone.step(69)
     np.testing.assert_array_equal(states[0][0], lone.state().cpu().numpy())
+
+
+def test_bounded_wait_runs_out_and_reports_timeout(B):
+    """The persistent launch's grid-barrier wait is bounded: a wait for an arrival that never comes
+    (the library's self-test, one block) runs out after its polls, sc_sync reports SC_ETIMEOUT once,
+    and the context's state and stepping are untouched (bit-equal to a context that never waited)."""
+    L = 32
+    kw = dict(G=2.5, G_self=(0.0, 0.0), tau=(1.0, 1.0))
+    f = S.droplet((L, L, L), (L // 2,) * 3, 8.0, n_in=0.85, n_out=0.15, amplitude=1e-3, seed=700)
+    p = B.make_params((L, L, L), lattice=B.SC_D3Q19, psi_self=B.SC_PSI_EXP, storage=B.SC_STORE_F32, **kw)
+    sim, ref = B.Simulation(p, *f), B.Simulation(p, *f)
+    sim.step(3)
+    B.sc_selftest_wait_timeout(sim.ctx, 4096)
+    with pytest.raises(B.ScError) as e:
+        sim.sync()
+    assert e.value.status == B.SC_ETIMEOUT
+    sim.sync()  # the flag was cleared
+    sim.step(5)
+    ref.step(8)
+    sim.sync()
+    ref.sync()
+    np.testing.assert_array_equal(sim.state().cpu().numpy(), ref.state().cpu().numpy())
