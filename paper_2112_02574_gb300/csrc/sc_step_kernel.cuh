@@ -70,12 +70,17 @@ __device__ __forceinline__ P2<CT> pull_site(const ST *__restrict__ src, int gx, 
 }
 
 // psi(n) - psi(nbar) per component; for psi = exp(-1/n): psibar * expm1((n - nbar) / (n nbar)).
+// psi of a component enters only its own self-coupling force term (Eq. sc_force), so a component
+// with G_JJ = 0 (gself 0) gets 0 instead: its force term is 0 either way, and the division and
+// expm1 are skipped (the branch is uniform: the couplings are the lattice's).
 template <class CT>
-__device__ __forceinline__ P2<CT> psi_deviation(P2<CT> dn, P2<CT> nbar, P2<CT> psibar, int psi_exp) {
+__device__ __forceinline__ P2<CT> psi_deviation(P2<CT> dn, P2<CT> nbar, P2<CT> psibar, int psi_exp, P2<CT> gself) {
   if (!psi_exp) return dn;
   const P2<CT> n = padd(nbar, dn);
   const P2<CT> q = pmul(n, nbar);
-  return pmul(psibar, pset(expm1_ct(rdiv(dn.x, q.x)), expm1_ct(rdiv(dn.y, q.y))));
+  const CT ex = gself.x != CT(0) ? expm1_ct(rdiv(dn.x, q.x)) : CT(0);
+  const CT ey = gself.y != CT(0) ? expm1_ct(rdiv(dn.y, q.y)) : CT(0);
+  return pmul(psibar, pset(ex, ey));
 }
 
 // Shared-memory bytes of one block: density and psi deviation pairs, a ring of
@@ -371,7 +376,7 @@ __device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by
       const P2<CT> dn =
           pull_site<LAT, ST, CT, KEEP>(src, gx, gy, gz, nx, ny, nz, N, a.scale, a.inv_scale, g, a.nsrc);
       s_dn[slot * PLANE + own] = dn;
-      if (a.self_on) s_psi[slot * PLANE + own] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp);
+      if (a.self_on) s_psi[slot * PLANE + own] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp, a.gself);
       if constexpr (KEEP) {
 #pragma unroll
         for (int q = 0; q + 1 < NC; ++q)
@@ -397,7 +402,7 @@ __device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by
           pull_site<LAT, ST, CT, false>(src, hx, hy, gz, nx, ny, nz, N, a.scale, a.inv_scale, nullptr, a.nsrc);
       const int idx = (py + H) * SX + (px + H);
       s_dn[slot * PLANE + idx] = dn;
-      if (a.self_on) s_psi[slot * PLANE + idx] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp);
+      if (a.self_on) s_psi[slot * PLANE + idx] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp, a.gself);
     }
     __syncthreads();
 

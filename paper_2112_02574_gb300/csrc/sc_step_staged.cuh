@@ -289,7 +289,7 @@ __device__ __forceinline__ void staged_block(const StepArgs<CT> &a, int bx, int 
       const P2<CT> dn = staged_sum<ST, CT, TY, true>(stage, nring, nsl, tx, ty, a.scale, a.inv_scale, g);
       make_carry<kD3Q19, CT, T1>(g, mine);
       s_dn[slot * G::PLANE + own] = dn;
-      if (a.self_on) s_psi[slot * G::PLANE + own] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp);
+      if (a.self_on) s_psi[slot * G::PLANE + own] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp, a.gself);
     }
 #pragma unroll
     for (int m = 0; m < NTASK; ++m) {
@@ -297,7 +297,7 @@ __device__ __forceinline__ void staged_block(const StepArgs<CT> &a, int bx, int 
         const P2<CT> dn =
             staged_sum<ST, CT, TY, false>(stage, nring, nsl, task_px[m], task_py[m], a.scale, a.inv_scale, nullptr);
         s_dn[slot * G::PLANE + task_idx[m]] = dn;
-        if (a.self_on) s_psi[slot * G::PLANE + task_idx[m]] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp);
+        if (a.self_on) s_psi[slot * G::PLANE + task_idx[m]] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp, a.gself);
       }
     }
     __syncthreads();  // stage s and density slot (k + NS + 2) & 3 fully read, ring plane and row pointers written
