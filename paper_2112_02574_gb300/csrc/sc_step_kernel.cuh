@@ -370,13 +370,36 @@ __device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by
   for (int m = 0; m < np; ++m) {
     const int p = down ? zend - 1 + HZ - m : z0 - HZ + m;
     const int gz = ((p % nz) + nz) % nz;
-    // ---- density / psi deviations of this plane: own site
-    {
+    if constexpr (NHALO <= NT) {
+      // ---- density / psi deviations of this plane: own site and (threads tid < NHALO) one halo
+      // site, both pulls issued before either sum is used so that their L2 latencies overlap;
+      // threads without a halo site pull their own site a second time and discard it
+      const bool hal = tid < NHALO;
+      int px = 0, py = 0;
+      if (tid < 2 * H * SX) {
+        const int r = tid / SX;
+        px = tid - r * SX - H;
+        py = r < H ? r - H : TY + (r - H);
+      } else {
+        const int k = tid - 2 * H * SX, r = k / (2 * H), c = k - r * (2 * H);
+        py = r;
+        px = c < H ? c - H : 32 + (c - H);
+      }
+      const int hx = hal ? ((x0 + px) % nx + nx) % nx : gx, hy = hal ? ((y0 + py) % ny + ny) % ny : gy;
+      const int idx = (py + H) * SX + (px + H);
       P2<CT> g[Q];
       const P2<CT> dn =
           pull_site<LAT, ST, CT, KEEP>(src, gx, gy, gz, nx, ny, nz, N, a.scale, a.inv_scale, g, a.nsrc);
+      const P2<CT> dh =
+          pull_site<LAT, ST, CT, false>(src, hx, hy, gz, nx, ny, nz, N, a.scale, a.inv_scale, nullptr, a.nsrc);
       s_dn[slot * PLANE + own] = dn;
-      if (a.self_on) s_psi[slot * PLANE + own] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp, a.gself);
+      if (hal) s_dn[slot * PLANE + idx] = dh;
+      if (a.self_on) {
+        const P2<CT> pn = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp, a.gself);
+        const P2<CT> ph = psi_deviation<CT>(dh, a.nbar, a.psibar, a.psi_exp, a.gself);
+        s_psi[slot * PLANE + own] = pn;
+        if (hal) s_psi[slot * PLANE + idx] = ph;
+      }
       if constexpr (KEEP) {
 #pragma unroll
         for (int q = 0; q + 1 < NC; ++q)
@@ -384,25 +407,41 @@ __device__ __forceinline__ void step_block(const StepArgs<CT> &a, int bx, int by
           for (int i = 0; i < CQ; ++i) car[q][i] = car[q + 1][i];
         make_carry<LAT, CT, T1>(g, car[NC - 1]);
       }
-    }
-    // ---- halo sites (full rows first, for coalescing, then the side columns)
-    for (int h = tid; h < NHALO; h += NT) {
-      int px, py;
-      if (h < 2 * H * SX) {
-        const int r = h / SX;
-        px = h - r * SX - H;
-        py = r < H ? r - H : TY + (r - H);
-      } else {
-        const int k = h - 2 * H * SX, r = k / (2 * H), c = k - r * (2 * H);
-        py = r;
-        px = c < H ? c - H : 32 + (c - H);
+    } else {
+      // ---- density / psi deviations of this plane: own site
+      {
+        P2<CT> g[Q];
+        const P2<CT> dn =
+            pull_site<LAT, ST, CT, KEEP>(src, gx, gy, gz, nx, ny, nz, N, a.scale, a.inv_scale, g, a.nsrc);
+        s_dn[slot * PLANE + own] = dn;
+        if (a.self_on) s_psi[slot * PLANE + own] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp, a.gself);
+        if constexpr (KEEP) {
+#pragma unroll
+          for (int q = 0; q + 1 < NC; ++q)
+#pragma unroll
+            for (int i = 0; i < CQ; ++i) car[q][i] = car[q + 1][i];
+          make_carry<LAT, CT, T1>(g, car[NC - 1]);
+        }
       }
-      const int hx = ((x0 + px) % nx + nx) % nx, hy = ((y0 + py) % ny + ny) % ny;
-      const P2<CT> dn =
-          pull_site<LAT, ST, CT, false>(src, hx, hy, gz, nx, ny, nz, N, a.scale, a.inv_scale, nullptr, a.nsrc);
-      const int idx = (py + H) * SX + (px + H);
-      s_dn[slot * PLANE + idx] = dn;
-      if (a.self_on) s_psi[slot * PLANE + idx] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp, a.gself);
+      // ---- halo sites (full rows first, for coalescing, then the side columns)
+      for (int h = tid; h < NHALO; h += NT) {
+        int px, py;
+        if (h < 2 * H * SX) {
+          const int r = h / SX;
+          px = h - r * SX - H;
+          py = r < H ? r - H : TY + (r - H);
+        } else {
+          const int k = h - 2 * H * SX, r = k / (2 * H), c = k - r * (2 * H);
+          py = r;
+          px = c < H ? c - H : 32 + (c - H);
+        }
+        const int hx = ((x0 + px) % nx + nx) % nx, hy = ((y0 + py) % ny + ny) % ny;
+        const P2<CT> dn =
+            pull_site<LAT, ST, CT, false>(src, hx, hy, gz, nx, ny, nz, N, a.scale, a.inv_scale, nullptr, a.nsrc);
+        const int idx = (py + H) * SX + (px + H);
+        s_dn[slot * PLANE + idx] = dn;
+        if (a.self_on) s_psi[slot * PLANE + idx] = psi_deviation<CT>(dn, a.nbar, a.psibar, a.psi_exp, a.gself);
+      }
     }
     __syncthreads();
 
