@@ -176,3 +176,29 @@ def test_bounded_wait_runs_out_and_reports_timeout(B):
     sim.sync()
     ref.sync()
     np.testing.assert_array_equal(sim.state().cpu().numpy(), ref.state().cpu().numpy())
+
+
+def test_tune_batch_times_both_launch_forms(B):
+    """The batch autotuner times every candidate block shape in both launch forms of a staged batch
+    (persistent, and one launch per step), returns (tile_y, tile_z, stages, blocks_per_sm, persistent),
+    and a batch with the tuned shape and form equals the default batch bit for bit."""
+    from paper_2112_02574_gb300 import tune
+
+    sets = []
+    for k, L in enumerate((32, 40)):
+        kw = dict(G=2.5, G_self=(0.0, 0.0) if k == 0 else (-0.4, 0.0), tau=(1.0, 1.0))
+        f = S.droplet((L, L, L), (L // 2,) * 3, L / 4, n_in=0.85, n_out=0.15, amplitude=1e-3, seed=800 + k)
+        sets.append((B.make_params((L, L, L), lattice=B.SC_D3Q19, psi_self=B.SC_PSI_EXP, storage=B.SC_STORE_F32,
+                                   **kw), f))
+    plist, fields = [x[0] for x in sets], [x[1] for x in sets]
+    cands = [(8, 0, 1, 3), (4, 0, 1, 3)]
+    best, ms, table = tune.tune_batch(plist, fields, cands, steps=32)
+    assert len(best) == 5 and best[:4] in cands and ms > 0
+    assert sorted(c for c, _ in table) == sorted(c + (p,) for c in cands for p in (True, False))
+    tuned = B.Batch([tune.with_config(p, best) for p in plist], fields)
+    tuned.persistent = best[4]
+    default = B.Batch(plist, fields)
+    tuned.step(40)
+    default.step(40)
+    for a, b in zip(tuned.members, default.members):
+        np.testing.assert_array_equal(a.state().cpu().numpy(), b.state().cpu().numpy())
