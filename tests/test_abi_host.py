@@ -69,6 +69,8 @@ def test_null_and_range_arguments(B):
     assert B.lib.sc_step(None, 1) == B.SC_EINVAL
     assert B.lib.sc_sync(None) == B.SC_EINVAL
     assert B.lib.sc_selftest_wait_timeout(None, 16) == B.SC_EINVAL
+    assert B.lib.sc_batch_set_persistent(None, 1) == B.SC_EINVAL
+    assert B.lib.sc_batch_variant(None) == 0
     assert B.lib.sc_step_config(None, None, 8) == B.SC_EINVAL
     assert B.lib.sc_sigma_minimum(None, 10, None, 3, 1.0, 2.0, 0.1, None, None) == B.SC_EINVAL
     p = B.make_params((8, 8, 8))
