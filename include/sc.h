@@ -310,11 +310,13 @@ sc_status sc_run_host_sigma(const sc_params *params, const double *nA0, const do
  * (variant 0 or 2, D3Q19, E4, nx >= 32 a multiple of the chunk sites; members
  * then share stages and blocks_per_sm), else the generic one; a member with
  * variant 2 in a batch that cannot be staged is an error (SC_EINVAL).
- * A staged batch runs 32 time steps of every member in ONE persistent
- * cooperative launch (its blocks take the work items of a step and meet at a
- * grid-wide barrier before the next; a barrier wait that runs out sets bit 1 of
- * every member's status word, reported by sc_sync as SC_ETIMEOUT); a generic
- * batch replays 32 chained launches, one per step.  Steps outside whole runs of
+ * By default (where the device has cooperative launch; see
+ * sc_batch_set_persistent) a staged batch runs 32 time steps of every member in
+ * ONE persistent cooperative launch: in each step its blocks draw the work
+ * items from a ticket counter, then meet at a grid-wide barrier before the
+ * next; a barrier wait that runs out (2^20 polls, a few seconds) sets bit 1 of
+ * every member's status word, reported by sc_sync as SC_ETIMEOUT.  Otherwise,
+ * and for a generic batch, the graph replays 32 chained launches, one per step.  Steps outside whole runs of
  * 32 are single launches.  Each member is an ordinary context for the analysis
  * entry points (sc_moments, sc_pressure_profile, sc_bulk_pressure_at, ...);
  * sc_step refuses batch members. */
